@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the sheared model-H step on GB300: prints ONE JSON line.
+
+Workload: a 4096 x 4096 inertial run in FP32 (rho = eta = 1, a = b = kappa = M = 1,
+dx = 1, gdot = 0.001, dt = 0.005) from the seeded +-0.01 quench, the large single
+run on which the metric (grid-point updates/s, FP32 against the same GPU's FP64
+path, and the fraction of the HBM roofline) is quoted.  A step is one full time
+step (six kernel launches).  The state plus scratch (448 MiB) exceeds L2, so no
+flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+N > 1 runs under torchrun: every rank advances its own replica of the workload
+(a single grid does not shard without all-to-all transposes; replicas only),
+the slowest rank's time is used, and `value` counts the points of all ranks.
+`--impl reference` times the FP64 CPU oracle instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "grid-point updates/s per GB300 (FP32 vs FP64, same GPU, at stated L2 error) + % HBM roofline"
+UNIT = "grid-point updates/s"
+NX = NY = 4096
+PARAMS = dict(a=1.0, b=1.0, kappa=1.0, M=1.0, eta=1.0, rho=1.0, gdot=0.001, dt=0.005)
+SEED, AMP = 0, 0.01
+FALLBACK_HBM_GBS = 6800.0
+# compulsory DRAM bytes per grid point of each launch, in units of one real
+# (4 B in FP32): fields read + fields written (an x-spectral field of nx/2
+# complex per row is one real per point)
+KERNEL_REALS_PER_POINT = {
+    "stage1_stencil_rowfft": 6,   # phi, psi, omega in; phi*, f, omega* (x-spectral) out
+    "colpass_phi": 3,             # phi*, f in; phi^{n+1} out
+    "rowinv_phi": 2,              # x-spectral phi in; real phi out
+    "stage2_stencil_rowfft": 2,   # phi in; g (x-spectral) out
+    "colpass_flow": 4,            # g, omega* in; psi, omega out
+    "rowinv_flow": 4,             # psi, omega (x-spectral) in; real psi, omega out
+}
+KERNEL_SOURCES = ["paper_0710_5912_gb300/csrc/step_kernels.cu", "paper_0710_5912_gb300/csrc/fft_block.cuh",
+                  "paper_0710_5912_gb300/csrc/shf_internal.cuh"]
+WORKLOAD = ("4096x4096 inertial model H, FP32 bulk with FP64 strain/phase/mass, rho=eta=1, a=b=kappa=M=1, "
+            "dx=1, gdot=0.001, dt=0.005, seeded +-0.01 quench")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def sources_sha():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(kernel):
+    """Per-launch DRAM bytes from the committed ncu summary of this kernel at this
+    size, if it was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{NX}x{NY}_fp32.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if ":" in line and line.strip().startswith(("dram_bytes_per_launch", "source_sha256")):
+                k, v = line.split(":", 1)
+                vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_sha256") != sources_sha():
+        return None
+    try:
+        return int(float(vals["dram_bytes_per_launch"]))
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.lines = []
+        self.proc = None
+
+    def _one(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            out = subprocess.run(cmd, capture_output=True, text=True, timeout=10).stdout
+            return [l for l in out.splitlines() if l.strip()][:1]
+        except Exception:
+            return []
+
+    def start(self):
+        self.lines += self._one()
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            if line.strip():
+                self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.reader.join(timeout=2)
+        self.lines += self._one()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def allreduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_oracle_step_rate(n, steps=1):
+    """Oracle (float64 numpy, one thread) on an n x n grid of the workload."""
+    import oracle
+    from paper_0710_5912_gb300 import inputs
+    p = oracle.Params(**PARAMS)
+    fields = inputs.quench_state(n, n, SEED, AMP)
+    t0 = time.perf_counter()
+    fields = oracle.run(*fields, steps, p)
+    dt = time.perf_counter() - t0
+    return n * n * steps / dt, dt
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    n_sample = 1024
+    for _ in range(args.warmup):
+        cpu_oracle_step_rate(n_sample, 1)
+    rate, secs = cpu_oracle_step_rate(n_sample, args.steps)
+    sample = (f"each step: one oracle step (float64 numpy, 1 thread) of the workload's scheme and "
+              f"parameters on a {n_sample}x{n_sample} grid; {args.steps} steps in {secs:.1f} s")
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, **PARAMS, "seed": SEED, "amp": AMP},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, local_rank, world = dist_env()
+    import numpy as np
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    import paper_0710_5912_gb300 as shf
+    shf.lib()
+
+    stream = torch.cuda.Stream()
+    g = shf.Grid(NX, NY, 1.0, shf.SHF_FP32, stream=stream)
+    g.set_params(**PARAMS)
+    g.init_noise(SEED + rank, AMP)
+    if args.warmup > 0:
+        g.profile_step(args.warmup)
+    g.sync()
+
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local_rank).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    kernel_ms = g.profile_step(args.steps)            # K steps, per-launch events on the grid's stream
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    elapsed_ms = allreduce_max(e0.elapsed_time(e1), world)
+    ms_per_step = elapsed_ms / args.steps
+    value = world * NX * NY * args.steps / (elapsed_ms / 1e3)
+    g.sync()
+
+    # graph-replay path (shf_step) over the same number of steps, for reference
+    torch.cuda.synchronize()
+    e0.record(stream)
+    g.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    graph_ms_per_step = e0.elapsed_time(e1) / args.steps
+
+    # roofline of the dominant kernel
+    peak, peak_src = measured_peaks()
+    dom = max(kernel_ms, key=kernel_ms.get)
+    alg_bytes = KERNEL_REALS_PER_POINT[dom] * 4 * NX * NY
+    achieved = alg_bytes / (kernel_ms[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": profiled_traffic(dom),
+                "algorithmic_bytes": alg_bytes, "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json)"
+                if peak_src == "measured" else "fallback 6.8 TB/s"}
+    step_bytes = sum(KERNEL_REALS_PER_POINT.values()) * 4 * NX * NY
+    kernels = {k: {"ms": v, "share": v / sum(kernel_ms.values()),
+                   "GBps": KERNEL_REALS_PER_POINT[k] * 4 * NX * NY / (v * 1e-3) / 1e9}
+               for k, v in kernel_ms.items()}
+
+    # end to end through the public API with host buffers (pinned), every step:
+    # H2D of phi, psi, omega (float64) + step + D2H of the new phi, psi, omega
+    e2e = None
+    if not args.no_e2e:
+        host = [torch.empty((NY, NX), dtype=torch.float64, pin_memory=True).numpy() for _ in range(3)]
+        phi0, psi0, om0 = g.get_fields()
+        host[0][:], host[1][:], host[2][:] = phi0, psi0, om0
+        E = max(1, min(args.steps, 20))
+        lib = shf.lib()
+        ptr = [h.ctypes.data_as(shf._native.P_double) for h in host]
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(E):
+            lib.shf_set_fields(g.handle, ptr[0], ptr[1], ptr[2])
+            lib.shf_step(g.handle, 1)
+            rc = lib.shf_get_fields(g.handle, ptr[0], ptr[1], ptr[2])
+            if rc != 0:
+                raise RuntimeError("e2e get_fields failed")
+        t_e2e = allreduce_max(time.perf_counter() - t0, world)
+        e2e = {"value": world * NX * NY * E / t_e2e, "unit": UNIT, "steps": E,
+               "h2d_bytes_per_step": 3 * 8 * NX * NY, "d2h_bytes_per_step": 3 * 8 * NX * NY,
+               "path": "shf_set_fields + shf_step(1) + shf_get_fields, float64 pinned host arrays"}
+    g.close()
+
+    # same-GPU FP64 path and the FP32 error against it after 200 steps
+    fp64 = None
+    if not args.no_fp64:
+        n_acc = 200
+        res = {}
+        for prec in (shf.SHF_FP64, shf.SHF_FP32):
+            h = shf.Grid(NX, NY, 1.0, prec, stream=stream)
+            h.set_params(**PARAMS)
+            h.init_noise(SEED, AMP)
+            h.profile_step(2)
+            h.set_step(0)
+            h.init_noise(SEED, AMP)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            h.step(n_acc)
+            e1.record(stream)
+            e1.synchronize()
+            res[prec] = (e0.elapsed_time(e1) / n_acc, h.get_fields())
+            h.close()
+        ms64 = res[shf.SHF_FP64][0]
+        errs = {}
+        for name, a, b in zip(("phi", "psi", "omega"), res[shf.SHF_FP32][1], res[shf.SHF_FP64][1]):
+            errs[name] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        fp64 = {"value": world * NX * NY / (allreduce_max(ms64, world) / 1e3), "unit": UNIT,
+                "ms_per_step": ms64, "fp32_over_fp64": (world * NX * NY / (ms_per_step / 1e3)) /
+                (world * NX * NY / (ms64 / 1e3)),
+                "fp32_vs_fp64_rel_l2_after_200_steps": errs,
+                "stated_tolerance": "FP32 <= 2e-5, FP64 <= 1e-10 relative L2 vs the FP64 oracle after 200 steps"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, secs = cpu_oracle_step_rate(NX, 1)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one full {NX}x{NY} step of the workload by the float64 numpy oracle, 1 thread, "
+                         f"{secs:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, **PARAMS, "seed": SEED, "amp": AMP,
+                           "parallelism": f"replicas x{world}" if world > 1 else "single grid",
+                           "l2": "state + scratch 448 MiB > L2: inputs larger than L2, no flush"},
+                "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e,
+                "gpu_launches": 6 * args.steps,
+                "graph_ms_per_step": graph_ms_per_step,
+                "step_algorithmic_bytes": step_bytes,
+                "step_hbm_frac": step_bytes / (ms_per_step * 1e-3) / 1e9 / peak,
+                "kernels": kernels, "fp64": fp64}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,258 @@
+// Diagnostics and data movement: precision conversion, the mass of phi
+// (compensated double-precision sums) and the structure factor S(q) with its
+// moments (Section VI, Eq. L_structure).  All reductions are deterministic:
+// fixed per-thread order, fixed tree order in the CTA, fixed order over CTAs.
+#include "shf_internal.cuh"
+
+namespace shf {
+
+// Neumaier's compensated summation (improved Kahan): sum holds the running
+// sum, comp the accumulated rounding error of every addition.
+__device__ __forceinline__ void neumaier_add(double& sum, double& comp, double v) {
+  const double t = sum + v;
+  if (fabs(sum) >= fabs(v)) comp += (sum - t) + v;
+  else comp += (v - t) + sum;
+  sum = t;
+}
+
+// Deterministic block reduction of NV (sum, comp) pairs (and plain values)
+// through warp shuffles and one shared-memory round.  Result valid in thread 0.
+template <int NV>
+__device__ void block_reduce_pairs(double (&s)[NV], double (&c)[NV], double* sh /* 2*NV*32 */) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const double os = __shfl_down_sync(0xffffffffu, s[v], off);
+      const double oc = __shfl_down_sync(0xffffffffu, c[v], off);
+      if (lane < off) {
+        neumaier_add(s[v], c[v], os);
+        c[v] += oc;
+      }
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      sh[(2 * v) * 32 + warp] = s[v];
+      sh[(2 * v + 1) * 32 + warp] = c[v];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      s[v] = sh[(2 * v) * 32];
+      c[v] = sh[(2 * v + 1) * 32];
+      for (int w = 1; w < nw; ++w) {
+        neumaier_add(s[v], c[v], sh[(2 * v) * 32 + w]);
+        c[v] += sh[(2 * v + 1) * 32 + w];
+      }
+    }
+  }
+}
+
+template <class T>
+__global__ void k_convert_in(const double* __restrict__ src, T* __restrict__ dst, long long count) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x)
+    dst[e] = (T)src[e];
+}
+template <class T>
+__global__ void k_convert_out(const T* __restrict__ src, double* __restrict__ dst, long long count) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x)
+    dst[e] = (double)src[e];
+}
+
+// out[3*cta + 0..2] = (sum, compensation, non-finite count) over this CTA's
+// grid-stride share of f.
+template <class T>
+__global__ void __launch_bounds__(256) k_mass_partials(const T* __restrict__ f, long long count,
+                                                       double* __restrict__ out) {
+  __shared__ double sh[2 * 2 * 32];
+  double s[2] = {0.0, 0.0}, c[2] = {0.0, 0.0};
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double v = (double)f[e];
+    if (isfinite(v)) neumaier_add(s[0], c[0], v);
+    else s[1] += 1.0;
+  }
+  block_reduce_pairs<2>(s, c, sh);
+  if (threadIdx.x == 0) {
+    out[3 * blockIdx.x + 0] = s[0];
+    out[3 * blockIdx.x + 1] = c[0];
+    out[3 * blockIdx.x + 2] = s[1] + c[1];
+  }
+}
+
+// Row transform of a real field, two rows per FFT (z = f_{2p} + i f_{2p+1}).
+template <class T>
+__global__ void __launch_bounds__(512) k_sf_rows(const T* __restrict__ f, cplx<T>* __restrict__ xs,
+                                                  int log2nx, int log2ny, const cplx<T>* __restrict__ tw) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nx = 1 << log2nx, mx = nx - 1, half = nx >> 1;
+  const int Tf = nx >> 3;
+  const int inst = threadIdx.x / Tf, tid = threadIdx.x - inst * Tf;
+  const int ipc = blockDim.x / Tf;
+  const int j0 = 2 * (blockIdx.x * ipc + inst);
+  C* z = reinterpret_cast<C*>(smem_raw) + (size_t)inst * nx;
+  for (int q = 0; q < 8; ++q) {
+    const int i = tid + q * Tf;
+    z[i] = C{f[(size_t)j0 * nx + i], f[(size_t)(j0 + 1) * nx + i]};
+  }
+  C* const b1[1] = {z};
+  fft_smem<false, 1>(b1, log2nx, tid, tw);
+  for (int q = 0; q < 4; ++q) {
+    const int k = tid + q * Tf;
+    const C zk = z[k], zc = cconj(z[(-k) & mx]);
+    xs[(size_t)j0 * half + k] = C{(zk.x + zc.x) * T(0.5), (zk.y + zc.y) * T(0.5)};
+    xs[(size_t)(j0 + 1) * half + k] = C{(zk.y - zc.y) * T(0.5), -(zk.x - zc.x) * T(0.5)};
+  }
+}
+
+// Column transforms of the x-spectral phi, then per-CTA partial moments of
+// S = |phi_hat|^2 / (nx ny)^2 over the laboratory wavevector magnitude
+// k = |(q_x, q_y - s q_x)|, half-spectrum weight 2 for m > 0, k = 0 and the
+// Nyquist row excluded; optional per-CTA bins of width dk = 2 pi / (ny dx).
+template <class T>
+__global__ void __launch_bounds__(512) k_sf_cols(const cplx<T>* __restrict__ xs, int log2nx, int log2ny,
+                                                  double dx, double s, const cplx<T>* __restrict__ tw,
+                                                  double* __restrict__ partials, int nbins,
+                                                  double* __restrict__ bin_partials) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double sh[2 * 3 * 32];
+  const int nx = 1 << log2nx, ny = 1 << log2ny, half = nx >> 1;
+  const int Tc = ny >> 3;
+  const int col = threadIdx.x / Tc, tid = threadIdx.x - col * Tc;
+  const int ncol = blockDim.x / Tc;
+  const int log2ncol = 31 - __clz(ncol);
+  const int m0 = blockIdx.x * ncol;
+  C* sm = reinterpret_cast<C*>(smem_raw);
+  double* Sw = reinterpret_cast<double*>(sm + ncol * ny);     // weighted S per mode
+  int* bin = reinterpret_cast<int*>(Sw + ncol * ny);
+  for (int e = threadIdx.x; e < ncol * ny; e += blockDim.x) {
+    const int c = e & (ncol - 1), n = e >> log2ncol;
+    sm[c * ny + n] = xs[(size_t)n * half + m0 + c];
+  }
+  C* const b1[1] = {sm + col * ny};
+  fft_smem<false, 1>(b1, log2ny, tid, tw);
+  const int m = m0 + col;
+  const double two_pi = 6.283185307179586476925286766559;
+  const double qx = two_pi * m / (nx * dx);
+  const double norm = 1.0 / ((double)nx * (double)ny);
+  const double dk = two_pi / (ny * dx);
+  double acc_s[3] = {0, 0, 0}, acc_c[3] = {0, 0, 0};
+  for (int q = 0; q < 8; ++q) {
+    const int n = tid + q * Tc;
+    const int idx = col * ny + n;
+    double w = 0.0;
+    int b = -1;
+    if (n != (ny >> 1) && !(m == 0 && n == 0)) {
+      const int ns = n < (ny >> 1) ? n : n - ny;
+      const double qy = two_pi * ns / (ny * dx);
+      const double ky = qy - s * qx;
+      const double k = sqrt(qx * qx + ky * ky);
+      const C X = sm[idx];
+      const double re = (double)X.x * norm, im = (double)X.y * norm;
+      const double S = (m == 0 ? 1.0 : 2.0) * (re * re + im * im);
+      neumaier_add(acc_s[0], acc_c[0], S);
+      neumaier_add(acc_s[1], acc_c[1], k * S);
+      neumaier_add(acc_s[2], acc_c[2], S / k);
+      w = S;
+      const double fb = floor(k / dk);
+      b = (fb < (double)nbins) ? (int)fb : -1;
+    }
+    if (nbins > 0) {
+      Sw[idx] = w;
+      bin[idx] = b;
+    }
+  }
+  block_reduce_pairs<3>(acc_s, acc_c, sh);
+  if (threadIdx.x == 0) {
+    for (int v = 0; v < 3; ++v) partials[3 * blockIdx.x + v] = acc_s[v] + acc_c[v];
+  }
+  if (nbins > 0) {
+    __syncthreads();
+    for (int bb = threadIdx.x; bb < nbins; bb += blockDim.x) {
+      double sum = 0.0, comp = 0.0;
+      for (int e = 0; e < ncol * ny; ++e)
+        if (bin[e] == bb) neumaier_add(sum, comp, Sw[e]);
+      bin_partials[(size_t)blockIdx.x * nbins + bb] = sum + comp;
+    }
+  }
+}
+
+// Column sums of a rows x cols array, each column summed over rows in order.
+__global__ void k_reduce_rows(const double* __restrict__ in, int rows, int cols, double* __restrict__ out) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= cols) return;
+  double sum = 0.0, comp = 0.0;
+  for (int r = 0; r < rows; ++r) neumaier_add(sum, comp, in[(size_t)r * cols + c]);
+  out[c] = sum + comp;
+}
+
+// ----------------------------------------------------------------- launchers
+template <class T>
+void launch_convert_in(const double* src, T* dst, long long count, cudaStream_t st) {
+  const int thr = 256;
+  long long ctas = (count + thr - 1) / thr;
+  if (ctas > 4096) ctas = 4096;
+  k_convert_in<T><<<(int)ctas, thr, 0, st>>>(src, dst, count);
+}
+template <class T>
+void launch_convert_out(const T* src, double* dst, long long count, cudaStream_t st) {
+  const int thr = 256;
+  long long ctas = (count + thr - 1) / thr;
+  if (ctas > 4096) ctas = 4096;
+  k_convert_out<T><<<(int)ctas, thr, 0, st>>>(src, dst, count);
+}
+template <class T>
+int launch_mass_partials(const T* f, long long count, double* out, int max_ctas, cudaStream_t st) {
+  const int thr = 256;
+  long long ctas = (count + thr - 1) / thr;
+  if (ctas > max_ctas) ctas = max_ctas;
+  if (ctas < 1) ctas = 1;
+  k_mass_partials<T><<<(int)ctas, thr, 0, st>>>(f, count, out);
+  return (int)ctas;
+}
+template <class T>
+void launch_sf_rows(const T* phi, cplx<T>* xs, int log2nx, int log2ny, const cplx<T>* tw, const RowCfg& c,
+                    cudaStream_t st) {
+  k_sf_rows<T><<<c.ctas, c.threads, c.smem, st>>>(phi, xs, log2nx, log2ny, tw);
+}
+template <class T>
+void launch_sf_cols(const cplx<T>* xs, int log2nx, int log2ny, double dx, double s, const cplx<T>* tw,
+                    const ColCfg& c, double* partials, int nbins, double* bin_partials, cudaStream_t st) {
+  k_sf_cols<T><<<c.ctas, c.threads, c.smem, st>>>(xs, log2nx, log2ny, dx, s, tw, partials, nbins,
+                                                  bin_partials);
+}
+void launch_reduce_rows(const double* in, int rows, int cols, double* out, cudaStream_t st) {
+  k_reduce_rows<<<(cols + 127) / 128, 128, 0, st>>>(in, rows, cols, out);
+}
+
+template <class T>
+void set_diag_smem_limits() {
+  const int lim = 220 * 1024;   // dynamic part; leaves room for static shared memory
+  cudaFuncSetAttribute(k_sf_rows<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_sf_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+}
+
+#define SHF_DIAG_INST(T)                                                                                   \
+  template void launch_convert_in<T>(const double*, T*, long long, cudaStream_t);                          \
+  template void launch_convert_out<T>(const T*, double*, long long, cudaStream_t);                         \
+  template int launch_mass_partials<T>(const T*, long long, double*, int, cudaStream_t);                   \
+  template void launch_sf_rows<T>(const T*, cplx<T>*, int, int, const cplx<T>*, const RowCfg&,             \
+                                  cudaStream_t);                                                           \
+  template void launch_sf_cols<T>(const cplx<T>*, int, int, double, double, const cplx<T>*, const ColCfg&, \
+                                  double*, int, double*, cudaStream_t);                                    \
+  template void set_diag_smem_limits<T>();
+
+SHF_DIAG_INST(float)
+SHF_DIAG_INST(double)
+
+}  // namespace shf

@@ -1,0 +1,164 @@
+// Block-level complex FFT in shared memory for the row and column passes.
+//
+// The paper's transforms (Appendix B: real <-> reciprocal space "x -> q_x and
+// y -> q_y", done with a CPU library) are done here by a hand-written
+// Stockham auto-sort FFT: every stage reads R values at stride N/R, applies the
+// stage twiddles, performs a radix-R DFT in registers and writes the results to
+// their auto-sorted positions, so the output comes out in natural order with no
+// bit reversal.  Each participating thread holds 8 complex values per buffer;
+// a stage is radix 8 (one butterfly per thread), or radix 4 / radix 2 for the
+// last stage when log2(N) is not a multiple of 3.
+//
+// Conventions (shared with the host code): forward uses exp(-2 pi i jk / N),
+// inverse uses exp(+2 pi i jk / N) without scaling.  Twiddles come from one
+// table W[k] = exp(+2 pi i k / NMAX), k < NMAX, computed on the host in double
+// precision and rounded once to the working precision; a length-N transform
+// reads it with stride NMAX / N.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace shf {
+
+constexpr int LOG2_NMAX = 12;          // largest supported transform: 4096 points
+constexpr int NMAX = 1 << LOG2_NMAX;
+
+template <class T> struct cplx_of;
+template <> struct cplx_of<float> { using type = float2; };
+template <> struct cplx_of<double> { using type = double2; };
+template <class T> using cplx = typename cplx_of<T>::type;
+
+template <class C> __device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+template <class C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+template <class C> __device__ __forceinline__ C cmul(C a, C b) {
+  return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <class C> __device__ __forceinline__ C cconj(C a) { return C{a.x, -a.y}; }
+template <class C, class T> __device__ __forceinline__ C cscale(C a, T s) { return C{a.x * s, a.y * s}; }
+
+// multiply by sigma*i, sigma = +1 (inverse) or -1 (forward)
+template <bool INV, class C> __device__ __forceinline__ C mul_si(C a) {
+  return INV ? C{-a.y, a.x} : C{a.y, -a.x};
+}
+
+template <bool INV, class C>
+__device__ __forceinline__ void dft2(C& a, C& b) {
+  C t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+// X_k = sum_r v_r w^{rk}, w = sigma*i
+template <bool INV, class C>
+__device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, C& v3) {
+  C s02 = cadd(v0, v2), d02 = csub(v0, v2);
+  C s13 = cadd(v1, v3), d13 = csub(v1, v3);
+  C wd = mul_si<INV>(d13);
+  v0 = cadd(s02, s13);
+  v2 = csub(s02, s13);
+  v1 = cadd(d02, wd);
+  v3 = csub(d02, wd);
+}
+
+// radix 8 as two radix-4 DFTs (even / odd inputs) joined by powers of
+// w8 = exp(sigma 2 pi i / 8) = (1 + sigma i) / sqrt(2)
+template <bool INV, class C>
+__device__ __forceinline__ void dft8(C* v) {
+  using T = decltype(v[0].x);
+  const T c = T(0.70710678118654752440084436210484904);  // 1/sqrt(2)
+  C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  const T sg = INV ? T(1) : T(-1);
+  // w8^1 * o1 = c (1 + sigma i) o1
+  C t1 = C{c * (o1.x - sg * o1.y), c * (o1.y + sg * o1.x)};
+  // w8^2 * o2 = sigma i o2
+  C t2 = mul_si<INV>(o2);
+  // w8^3 * o3 = c (-1 + sigma i) o3
+  C t3 = C{c * (-o3.x - sg * o3.y), c * (-o3.y + sg * o3.x)};
+  v[0] = cadd(e0, o0);
+  v[4] = csub(e0, o0);
+  v[1] = cadd(e1, t1);
+  v[5] = csub(e1, t1);
+  v[2] = cadd(e2, t2);
+  v[6] = csub(e2, t2);
+  v[3] = cadd(e3, t3);
+  v[7] = csub(e3, t3);
+}
+
+template <bool INV, class C>
+__device__ __forceinline__ C twiddle(const C* __restrict__ tw, int idx) {
+  C w = __ldg(tw + idx);
+  return INV ? w : cconj(w);
+}
+
+// One Stockham stage of radix R = 2^LR on NB buffers: each thread does 8/R
+// butterflies j = tid + b*T (T = N/8 threads per instance), reading inputs at
+// j + r*N/R and writing the radix-R outputs to ((j - k) R + k) + r Ns with
+// k = j mod Ns, Ns being the length of the sub-transforms already done.
+template <bool INV, int NB, int LR, class C>
+__device__ __forceinline__ void fft_stage(C* const (&buf)[NB], int log2N, int log2Ns, int tid,
+                                          const C* __restrict__ tw) {
+  constexpr int R = 1 << LR;
+  constexpr int B = 8 >> LR;
+  const int N = 1 << log2N;
+  const int T = N >> 3;
+  const int stride = N >> LR;
+  C v[NB][8];
+#pragma unroll
+  for (int q = 0; q < NB; ++q)
+#pragma unroll
+    for (int b = 0; b < B; ++b)
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q][b * R + r] = buf[q][tid + b * T + r * stride];
+  __syncthreads();
+  const int Ns = 1 << log2Ns;
+  const int twShift = LOG2_NMAX - log2Ns - LR;
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int j = tid + b * T;
+    const int k = j & (Ns - 1);
+    const int base = ((j - k) << LR) + k;
+    if (log2Ns > 0) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const C w = twiddle<INV>(tw, (k * r) << twShift);
+#pragma unroll
+        for (int q = 0; q < NB; ++q) v[q][b * R + r] = cmul(v[q][b * R + r], w);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      if (LR == 3) {
+        dft8<INV>(&v[q][b * R]);
+      } else if (LR == 2) {
+        dft4<INV>(v[q][b * R], v[q][b * R + 1], v[q][b * R + 2], v[q][b * R + 3]);
+      } else {
+        dft2<INV>(v[q][b * R], v[q][b * R + 1]);
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[q][base + r * Ns] = v[q][b * R + r];
+    }
+  }
+  __syncthreads();
+}
+
+// In-place FFT of NB buffers of length N = 2^log2N (N >= 8) held in shared
+// memory.  tid in [0, N/8) is this thread's index within its FFT instance;
+// every thread of the CTA must call this (it contains __syncthreads), and all
+// instances in the CTA must share N.  The routine starts with a barrier, so
+// the caller's writes to the buffers need no barrier of their own, and it
+// ends with one, so the results may be read right away.
+template <bool INV, int NB, class C>
+__device__ void fft_smem(C* const (&buf)[NB], int log2N, int tid, const C* __restrict__ tw) {
+  __syncthreads();
+  int log2Ns = 0;
+  while (log2N - log2Ns >= 3) {
+    fft_stage<INV, NB, 3>(buf, log2N, log2Ns, tid, tw);
+    log2Ns += 3;
+  }
+  if (log2N - log2Ns == 2) fft_stage<INV, NB, 2>(buf, log2N, log2Ns, tid, tw);
+  else if (log2N - log2Ns == 1) fft_stage<INV, NB, 1>(buf, log2N, log2Ns, tid, tw);
+}
+
+}  // namespace shf

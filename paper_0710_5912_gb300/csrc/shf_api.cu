@@ -1,0 +1,996 @@
+// Host side of the C ABI declared in include/shf.h: grid and ensemble objects,
+// device memory, launch configuration, per-step orchestration (six launches
+// per step and size class; runs of 100 steps are replayed from a captured CUDA
+// graph), conversions, diagnostics and checkpoints.
+#include <cmath>
+#include <cstdio>
+#include <cstddef>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/shf.h"
+#include "shf_internal.cuh"
+
+using namespace shf;
+
+namespace {
+
+constexpr int kVersion = 10000;        // 1.0.0
+constexpr size_t kSmemLimit = 220 * 1024;
+constexpr int kGraphSteps = 100;
+constexpr int kMassCtas = 1024;
+
+struct Member {
+  int nx = 0, ny = 0, log2nx = 0, log2ny = 0;
+  double dx = 1.0;
+  double a = 1, b = 1, kappa = 1, M = 1, eta = 1, rho = 1, gdot = 0, dt = 0;
+  bool params_set = false;
+  void* phi = nullptr;
+  void* psi = nullptr;
+  void* omega = nullptr;
+  bool bound = false;
+  void* xs[4] = {nullptr, nullptr, nullptr, nullptr};
+  long long* d_n = nullptr;   // into the owner's counter array
+  int cls = -1, slot = -1;
+};
+
+struct SizeClass {
+  int nx = 0, ny = 0, log2nx = 0, log2ny = 0;
+  std::vector<int> members;
+  std::vector<MemberDesc> h_desc;
+  MemberDesc* d_desc = nullptr;
+  RowCfg stage1{}, rowinv0{}, rowinv1{}, stage2{}, sfrows{};
+  ColCfg colphi{}, colflow{}, sfcols{};
+};
+
+int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+bool pow2_in_range(int v) { return v >= 8 && v <= NMAX && (v & (v - 1)) == 0; }
+
+}  // namespace
+
+struct shf_grid {
+  int kind = 0;                 // 0 grid, 1 ensemble, 2 member view
+  shf_grid* parent = nullptr;   // views: the ensemble
+  int member = 0;               // views: index into parent->members
+  int precision = SHF_FP32;
+  int remap_mode = SHF_REMAP_SHIFT;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<Member> members;
+  std::vector<SizeClass> classes;
+  long long* d_counters = nullptr;
+  long long n = 0;
+  void* d_tw = nullptr;
+  double* d_stage = nullptr;
+  size_t stage_count = 0;
+  double* d_scratch = nullptr;
+  size_t scratch_count = 0;
+  double* h_pinned = nullptr;
+  size_t pinned_count = 0;
+  cudaGraphExec_t graph = nullptr;
+  std::vector<shf_grid*> views;
+  std::string err;
+};
+
+namespace {
+
+int fail(shf_grid* g, int code, const std::string& msg) {
+  if (g) g->err = msg;
+  return code;
+}
+
+#define SHF_CUDA(g, call)                                                                  \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail((g), SHF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));      \
+  } while (0)
+
+shf_grid* owner(shf_grid* g) { return g->kind == 2 ? g->parent : g; }
+
+// (cos, sin)(2 pi k / N) by reduction to the first octant, so that the table
+// is exactly symmetric (W[N/4] = i, W[N/2] = -1, ...).
+void unit_root(long k, long N, double* c, double* s) {
+  k %= N;
+  if (k < 0) k += N;
+  const long q = k / (N / 4), r = k % (N / 4);
+  const double two_pi = 6.283185307179586476925286766559;
+  double cr, sr;
+  if (8 * r > N) {
+    const double th = two_pi * (double)(N / 4 - r) / (double)N;
+    cr = std::sin(th);
+    sr = std::cos(th);
+  } else {
+    const double th = two_pi * (double)r / (double)N;
+    cr = std::cos(th);
+    sr = std::sin(th);
+  }
+  switch (q) {
+    case 0: *c = cr; *s = sr; break;
+    case 1: *c = -sr; *s = cr; break;
+    case 2: *c = -cr; *s = -sr; break;
+    default: *c = sr; *s = -cr; break;
+  }
+}
+
+RowCfg row_cfg(int nx, int ny, int instances, size_t bytes_per_inst) {
+  RowCfg c{};
+  const int Tf = nx / 8;
+  int ipc = 256 / Tf;
+  if (ipc < 1) ipc = 1;
+  if (ipc > ny / 2) ipc = ny / 2;
+  while (ipc > 1 && ipc * bytes_per_inst > kSmemLimit) ipc /= 2;
+  c.inst_per_cta = ipc;
+  c.threads = ipc * Tf;
+  c.ctas = (instances + ipc - 1) / ipc;
+  c.smem = ipc * bytes_per_inst;
+  return c;
+}
+
+ColCfg col_cfg(int nx, int ny, size_t bytes_per_row_per_col, size_t elem, int max_threads) {
+  ColCfg c{};
+  const int Tc = ny / 8;
+  int cmin = (int)(32 / elem);
+  if (cmin < 1) cmin = 1;
+  int C = 256 / Tc;
+  if (C < cmin) C = cmin;
+  if (C > nx / 2) C = nx / 2;
+  while (C > 1 && ((size_t)C * ny * bytes_per_row_per_col > kSmemLimit || C * Tc > max_threads)) C /= 2;
+  c.cols_per_cta = C;
+  c.threads = C * Tc;
+  c.ctas = (nx / 2) / C;
+  c.smem = (size_t)C * ny * bytes_per_row_per_col;
+  return c;
+}
+
+void configure_class(SizeClass& cl, int precision) {
+  const size_t R = precision == SHF_FP64 ? 8 : 4;   // real
+  const size_t Cx = 2 * R;                            // complex
+  const int nx = cl.nx, ny = cl.ny;
+  cl.stage1 = row_cfg(nx, ny, ny / 2, 3 * nx * Cx);
+  cl.rowinv0 = row_cfg(nx, ny, ny / 2, nx * Cx);
+  cl.rowinv1 = row_cfg(nx, ny, ny, nx * Cx);
+  cl.stage2 = row_cfg(nx, ny, ny / 2, nx * (Cx + 4 * R));
+  cl.sfrows = row_cfg(nx, ny, ny / 2, nx * Cx);
+  const int colmax = precision == SHF_FP64 ? 512 : 1024;   // matches the kernels' launch bounds
+  cl.colphi = col_cfg(nx, ny, 2 * Cx, Cx, colmax);
+  cl.colflow = col_cfg(nx, ny, 2 * Cx, Cx, colmax);
+  cl.sfcols = col_cfg(nx, ny, Cx + 12, Cx, 512);
+}
+
+void host_strain(long long n, double gdot, double dt, int r, double* s, long long* K) {
+  volatile double total = (gdot * dt) * (double)n;
+  volatile double q = total / (double)r + 0.5;
+  const double Kd = std::floor(q);
+  volatile double kr = Kd * (double)r;
+  *s = total - kr;
+  *K = (long long)Kd;
+}
+
+MemberDesc make_desc(const shf_grid* o, const Member& m) {
+  MemberDesc d{};
+  d.phi = m.phi;
+  d.psi = m.psi;
+  d.omega = m.omega;
+  d.xs_phi = m.xs[0];
+  d.xs_f = m.xs[1];
+  d.xs_w = m.xs[2];
+  d.xs_g = m.xs[3];
+  d.n = m.d_n;
+  d.a = m.a; d.b = m.b; d.kappa = m.kappa; d.M = m.M; d.eta = m.eta; d.rho = m.rho;
+  d.gdot = m.gdot; d.dt = m.dt; d.dx = m.dx;
+  d.c_dt_aM = (m.dt * m.a) * m.M;
+  d.c_dt_bM = (m.dt * m.b) * m.M;
+  d.c_hdt_kM = 0.5 * ((m.dt * m.kappa) * m.M);
+  d.stokes = m.rho == 0.0 ? 1 : 0;
+  d.c_hdt_nu = d.stokes ? 0.0 : 0.5 * (m.dt * (m.eta / m.rho));
+  d.c_force = d.stokes ? -1.0 / m.eta : -1.0 / m.rho;
+  d.inv_2h = 1.0 / (2.0 * m.dx);
+  d.inv_h2 = 1.0 / (m.dx * m.dx);
+  d.inv_4h2 = 1.0 / (4.0 * m.dx * m.dx);
+  d.inv_nxny = 1.0 / ((double)m.nx * (double)m.ny);
+  const double two_pi = 6.283185307179586476925286766559;
+  d.qx_unit = two_pi / (m.nx * m.dx);
+  d.qy_unit = two_pi / (m.ny * m.dx);
+  d.remap = o->remap_mode == SHF_REMAP_SHIFT ? 1 : 0;
+  d.ratio = m.nx / m.ny;
+  return d;
+}
+
+int upload_desc(shf_grid* o, int mi) {
+  Member& m = o->members[mi];
+  SizeClass& cl = o->classes[m.cls];
+  cl.h_desc[m.slot] = make_desc(o, m);
+  SHF_CUDA(o, cudaMemcpyAsync(cl.d_desc + m.slot, &cl.h_desc[m.slot], sizeof(MemberDesc),
+                              cudaMemcpyHostToDevice, o->stream));
+  return SHF_OK;
+}
+
+size_t real_size(const shf_grid* o) { return o->precision == SHF_FP64 ? 8 : 4; }
+
+int ensure_stage(shf_grid* o, size_t count) {
+  if (o->stage_count >= count) return SHF_OK;
+  if (o->d_stage) cudaFree(o->d_stage);
+  o->d_stage = nullptr;
+  o->stage_count = 0;
+  if (cudaMalloc(&o->d_stage, count * sizeof(double)) != cudaSuccess)
+    return fail(o, SHF_ENOMEM, "staging buffer allocation failed");
+  o->stage_count = count;
+  return SHF_OK;
+}
+
+int ensure_scratch(shf_grid* o, size_t count) {
+  if (o->scratch_count >= count) return SHF_OK;
+  if (o->d_scratch) cudaFree(o->d_scratch);
+  o->d_scratch = nullptr;
+  o->scratch_count = 0;
+  if (cudaMalloc(&o->d_scratch, count * sizeof(double)) != cudaSuccess)
+    return fail(o, SHF_ENOMEM, "scratch allocation failed");
+  o->scratch_count = count;
+  return SHF_OK;
+}
+
+int ensure_pinned(shf_grid* o, size_t count) {
+  if (o->pinned_count >= count) return SHF_OK;
+  if (o->h_pinned) cudaFreeHost(o->h_pinned);
+  o->h_pinned = nullptr;
+  o->pinned_count = 0;
+  if (cudaMallocHost(&o->h_pinned, count * sizeof(double)) != cudaSuccess)
+    return fail(o, SHF_ENOMEM, "pinned host allocation failed");
+  o->pinned_count = count;
+  return SHF_OK;
+}
+
+void free_all(shf_grid* g) {
+  if (!g) return;
+  cudaSetDevice(g->device);
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  if (g->graph) cudaGraphExecDestroy(g->graph);
+  for (auto& m : g->members) {
+    if (!m.bound) {
+      cudaFree(m.phi);
+      cudaFree(m.psi);
+      cudaFree(m.omega);
+    }
+    for (void* p : m.xs) cudaFree(p);
+  }
+  for (auto& cl : g->classes) cudaFree(cl.d_desc);
+  cudaFree(g->d_counters);
+  cudaFree(g->d_tw);
+  cudaFree(g->d_stage);
+  cudaFree(g->d_scratch);
+  if (g->h_pinned) cudaFreeHost(g->h_pinned);
+  if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+  for (auto* v : g->views) delete v;
+  delete g;
+}
+
+int validate_size(shf_grid* g, int nx, int ny, double dx) {
+  if (!pow2_in_range(nx) || !pow2_in_range(ny))
+    return fail(g, SHF_EINVAL, "nx and ny must be powers of two in [8, 4096]");
+  if (nx % ny != 0) return fail(g, SHF_EINVAL, "ny must divide nx");
+  if (!(dx > 0.0) || !std::isfinite(dx)) return fail(g, SHF_EINVAL, "dx must be positive and finite");
+  return SHF_OK;
+}
+
+int validate_params(shf_grid* g, double a, double b, double kappa, double M, double eta, double rho, double gdot,
+                    double dt) {
+  const double all[8] = {a, b, kappa, M, eta, rho, gdot, dt};
+  for (double v : all)
+    if (!std::isfinite(v)) return fail(g, SHF_EINVAL, "parameters must be finite");
+  if (!(kappa > 0) || !(M > 0) || !(eta > 0) || !(dt > 0))
+    return fail(g, SHF_EINVAL, "kappa, M, eta and dt must be positive");
+  if (rho < 0) return fail(g, SHF_EINVAL, "rho must be >= 0");
+  return SHF_OK;
+}
+
+// Builds an object with the given member sizes; allocates everything.
+int build(shf_grid* g, const std::vector<int>& nx, const std::vector<int>& ny, const std::vector<double>& dx) {
+  SHF_CUDA(g, cudaGetDevice(&g->device));
+  if (!g->stream) {
+    SHF_CUDA(g, cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
+    g->own_stream = true;
+  }
+  if (g->precision == SHF_FP64) {
+    set_step_smem_limits<double>();
+    set_diag_smem_limits<double>();
+  } else {
+    set_step_smem_limits<float>();
+    set_diag_smem_limits<float>();
+  }
+  SHF_CUDA(g, cudaGetLastError());
+  const int nm = (int)nx.size();
+  g->members.resize(nm);
+  if (cudaMalloc(&g->d_counters, nm * sizeof(long long)) != cudaSuccess)
+    return fail(g, SHF_ENOMEM, "counter allocation failed");
+  SHF_CUDA(g, cudaMemsetAsync(g->d_counters, 0, nm * sizeof(long long), g->stream));
+  const size_t R = real_size(g);
+  for (int r = 0; r < nm; ++r) {
+    Member& m = g->members[r];
+    m.nx = nx[r];
+    m.ny = ny[r];
+    m.log2nx = ilog2(m.nx);
+    m.log2ny = ilog2(m.ny);
+    m.dx = dx[r];
+    m.d_n = g->d_counters + r;
+    const size_t bytes = (size_t)m.nx * m.ny * R;
+    void** bufs[7] = {&m.phi, &m.psi, &m.omega, &m.xs[0], &m.xs[1], &m.xs[2], &m.xs[3]};
+    for (void** p : bufs) {
+      if (cudaMalloc(p, bytes) != cudaSuccess) return fail(g, SHF_ENOMEM, "field allocation failed");
+      SHF_CUDA(g, cudaMemsetAsync(*p, 0, bytes, g->stream));
+    }
+    int found = -1;
+    for (size_t c = 0; c < g->classes.size(); ++c)
+      if (g->classes[c].nx == m.nx && g->classes[c].ny == m.ny) found = (int)c;
+    if (found < 0) {
+      SizeClass cl;
+      cl.nx = m.nx;
+      cl.ny = m.ny;
+      cl.log2nx = m.log2nx;
+      cl.log2ny = m.log2ny;
+      configure_class(cl, g->precision);
+      g->classes.push_back(cl);
+      found = (int)g->classes.size() - 1;
+    }
+    m.cls = found;
+    m.slot = (int)g->classes[found].members.size();
+    g->classes[found].members.push_back(r);
+  }
+  for (auto& cl : g->classes) {
+    cl.h_desc.resize(cl.members.size());
+    if (cudaMalloc(&cl.d_desc, cl.members.size() * sizeof(MemberDesc)) != cudaSuccess)
+      return fail(g, SHF_ENOMEM, "descriptor allocation failed");
+  }
+  for (int r = 0; r < nm; ++r) {
+    int rc = upload_desc(g, r);
+    if (rc) return rc;
+  }
+  // twiddle table W[k] = exp(2 pi i k / NMAX) in the working precision
+  std::vector<double> tw(2 * NMAX);
+  for (int k = 0; k < NMAX; ++k) unit_root(k, NMAX, &tw[2 * k], &tw[2 * k + 1]);
+  if (g->precision == SHF_FP64) {
+    if (cudaMalloc(&g->d_tw, NMAX * sizeof(double2)) != cudaSuccess) return fail(g, SHF_ENOMEM, "twiddles");
+    SHF_CUDA(g, cudaMemcpy(g->d_tw, tw.data(), NMAX * sizeof(double2), cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> twf(2 * NMAX);
+    for (int k = 0; k < 2 * NMAX; ++k) twf[k] = (float)tw[k];
+    if (cudaMalloc(&g->d_tw, NMAX * sizeof(float2)) != cudaSuccess) return fail(g, SHF_ENOMEM, "twiddles");
+    SHF_CUDA(g, cudaMemcpy(g->d_tw, twf.data(), NMAX * sizeof(float2), cudaMemcpyHostToDevice));
+  }
+  SHF_CUDA(g, cudaStreamSynchronize(g->stream));
+  return SHF_OK;
+}
+
+// The six launches of one step for one size class, in order (kind 0..5).
+template <class T>
+void launch_kind(shf_grid* o, SizeClass& cl, int kind) {
+  const cplx<T>* tw = static_cast<const cplx<T>*>(o->d_tw);
+  const int nm = (int)cl.members.size();
+  switch (kind) {
+    case 0: launch_stage1<T>(cl.d_desc, nm, cl.log2nx, cl.log2ny, tw, cl.stage1, o->stream); break;
+    case 1: launch_colpass_phi<T>(cl.d_desc, nm, cl.log2nx, cl.log2ny, tw, cl.colphi, o->stream); break;
+    case 2: launch_rowinv<T>(cl.d_desc, nm, cl.log2nx, cl.log2ny, tw, cl.rowinv0, 0, o->stream); break;
+    case 3: launch_stage2<T>(cl.d_desc, nm, cl.log2nx, cl.log2ny, tw, cl.stage2, o->stream); break;
+    case 4: launch_colpass_flow<T>(cl.d_desc, nm, cl.log2nx, cl.log2ny, tw, cl.colflow, o->stream); break;
+    default: launch_rowinv<T>(cl.d_desc, nm, cl.log2nx, cl.log2ny, tw, cl.rowinv1, 1, o->stream); break;
+  }
+}
+
+constexpr int kKinds = 6;
+
+template <class T>
+void enqueue_step(shf_grid* o) {
+  for (auto& cl : o->classes)
+    for (int k = 0; k < kKinds; ++k) launch_kind<T>(o, cl, k);
+}
+
+void enqueue_steps(shf_grid* o, long long k) {
+  for (long long i = 0; i < k; ++i) {
+    if (o->precision == SHF_FP64) enqueue_step<double>(o);
+    else enqueue_step<float>(o);
+  }
+}
+
+Member* member_of(shf_grid* g) {
+  if (g->kind == 2) return &g->parent->members[g->member];
+  if (g->kind == 0) return &g->members[0];
+  return nullptr;
+}
+
+int member_index(shf_grid* g) { return g->kind == 2 ? g->member : 0; }
+
+// sum of mass partials in fixed order; returns (sum, nonfinite count)
+template <class T>
+int field_sum(shf_grid* o, const Member& m, const void* field, double* total, double* nonfinite) {
+  int rc = ensure_scratch(o, 3 * kMassCtas);
+  if (rc) return rc;
+  rc = ensure_pinned(o, 3 * kMassCtas);
+  if (rc) return rc;
+  const long long count = (long long)m.nx * m.ny;
+  const int ctas = launch_mass_partials<T>(static_cast<const T*>(field), count, o->d_scratch, kMassCtas, o->stream);
+  SHF_CUDA(o, cudaGetLastError());
+  SHF_CUDA(o, cudaMemcpyAsync(o->h_pinned, o->d_scratch, 3 * ctas * sizeof(double), cudaMemcpyDeviceToHost,
+                              o->stream));
+  SHF_CUDA(o, cudaStreamSynchronize(o->stream));
+  double s = 0.0, c = 0.0, nf = 0.0;
+  for (int b = 0; b < ctas; ++b) {
+    const double v = o->h_pinned[3 * b];
+    const double t = s + v;
+    if (std::fabs(s) >= std::fabs(v)) c += (s - t) + v;
+    else c += (v - t) + s;
+    s = t;
+    c += o->h_pinned[3 * b + 1];
+    nf += o->h_pinned[3 * b + 2];
+  }
+  *total = s + c;
+  *nonfinite = nf;
+  return SHF_OK;
+}
+
+uint32_t crc32_update(uint32_t crc, const unsigned char* p, size_t len) {
+  // CRC-32 (IEEE 802.3, reflected polynomial 0xEDB88320), bitwise
+  crc = ~crc;
+  for (size_t i = 0; i < len; ++i) {
+    crc ^= p[i];
+    for (int k = 0; k < 8; ++k) crc = (crc >> 1) ^ (0xEDB88320u & (0u - (crc & 1u)));
+  }
+  return ~crc;
+}
+
+struct CkptHeader {
+  char magic[8];
+  uint32_t version;
+  int32_t nx, ny, precision, remap_mode, has_params;
+  double params[9];
+  int64_t n;
+  uint32_t payload_crc;
+  uint32_t header_crc;
+};
+
+}  // namespace
+
+namespace {
+
+template <class T>
+int set_fields_t(shf_grid* g, const double* phi, const double* psi, const double* omega) {
+  shf_grid* o = owner(g);
+  Member& m = *member_of(g);
+  const size_t count = (size_t)m.nx * m.ny;
+  const double* src[3] = {phi, psi, m.rho > 0 ? omega : nullptr};
+  void* dst[3] = {m.phi, m.psi, m.omega};
+  for (int f = 0; f < 3; ++f) {
+    if (!src[f]) {
+      SHF_CUDA(g, cudaMemsetAsync(dst[f], 0, count * sizeof(T), o->stream));
+      continue;
+    }
+    if (sizeof(T) == sizeof(double)) {
+      SHF_CUDA(g, cudaMemcpyAsync(dst[f], src[f], count * sizeof(double), cudaMemcpyHostToDevice, o->stream));
+    } else {
+      int rc = ensure_stage(o, count);
+      if (rc) return fail(g, rc, o->err);
+      SHF_CUDA(g, cudaMemcpyAsync(o->d_stage, src[f], count * sizeof(double), cudaMemcpyHostToDevice, o->stream));
+      launch_convert_in<T>(o->d_stage, static_cast<T*>(dst[f]), (long long)count, o->stream);
+      SHF_CUDA(g, cudaGetLastError());
+    }
+  }
+  SHF_CUDA(g, cudaStreamSynchronize(o->stream));
+  return SHF_OK;
+}
+
+template <class T>
+int get_fields_t(shf_grid* g, double* phi, double* psi, double* omega) {
+  shf_grid* o = owner(g);
+  Member& m = *member_of(g);
+  const size_t count = (size_t)m.nx * m.ny;
+  double* dst[3] = {phi, psi, omega};
+  const void* src[3] = {m.phi, m.psi, m.omega};
+  for (int f = 0; f < 3; ++f) {
+    if (!dst[f]) continue;
+    if (f == 2 && m.rho == 0.0) {
+      std::memset(dst[f], 0, count * sizeof(double));
+      continue;
+    }
+    if (sizeof(T) == sizeof(double)) {
+      SHF_CUDA(g, cudaMemcpyAsync(dst[f], src[f], count * sizeof(double), cudaMemcpyDeviceToHost, o->stream));
+    } else {
+      int rc = ensure_stage(o, count);
+      if (rc) return fail(g, rc, o->err);
+      launch_convert_out<T>(static_cast<const T*>(src[f]), o->d_stage, (long long)count, o->stream);
+      SHF_CUDA(g, cudaGetLastError());
+      SHF_CUDA(g, cudaMemcpyAsync(dst[f], o->d_stage, count * sizeof(double), cudaMemcpyDeviceToHost, o->stream));
+    }
+    SHF_CUDA(g, cudaStreamSynchronize(o->stream));
+  }
+  SHF_CUDA(g, cudaStreamSynchronize(o->stream));
+  return SHF_OK;
+}
+
+template <class T>
+int sf_t(shf_grid* g, double* S_binned, int nbins, double moments[5]) {
+  shf_grid* o = owner(g);
+  Member& m = *member_of(g);
+  SizeClass& cl = o->classes[m.cls];
+  double s;
+  long long K;
+  host_strain(o->n, m.gdot, m.dt, m.nx / m.ny, &s, &K);
+  const ColCfg& cc = cl.sfcols;
+  const size_t need = (size_t)cc.ctas * 3 + 3 + (size_t)cc.ctas * nbins + nbins;
+  int rc = ensure_scratch(o, need);
+  if (rc) return fail(g, rc, o->err);
+  rc = ensure_pinned(o, 3 + nbins);
+  if (rc) return fail(g, rc, o->err);
+  double* parts = o->d_scratch;
+  double* red = parts + (size_t)cc.ctas * 3;
+  double* bparts = red + 3;
+  double* bred = bparts + (size_t)cc.ctas * nbins;
+  const cplx<T>* tw = static_cast<const cplx<T>*>(o->d_tw);
+  cplx<T>* xs = static_cast<cplx<T>*>(m.xs[1]);
+  launch_sf_rows<T>(static_cast<const T*>(m.phi), xs, cl.log2nx, cl.log2ny, tw, cl.sfrows, o->stream);
+  launch_sf_cols<T>(xs, cl.log2nx, cl.log2ny, m.dx, s, tw, cc, parts, nbins, bparts, o->stream);
+  launch_reduce_rows(parts, cc.ctas, 3, red, o->stream);
+  if (nbins > 0) launch_reduce_rows(bparts, cc.ctas, nbins, bred, o->stream);
+  SHF_CUDA(g, cudaGetLastError());
+  SHF_CUDA(g, cudaMemcpyAsync(o->h_pinned, red, 3 * sizeof(double), cudaMemcpyDeviceToHost, o->stream));
+  if (nbins > 0)
+    SHF_CUDA(g, cudaMemcpyAsync(o->h_pinned + 3, bred, nbins * sizeof(double), cudaMemcpyDeviceToHost, o->stream));
+  SHF_CUDA(g, cudaStreamSynchronize(o->stream));
+  const double S0 = o->h_pinned[0], S1 = o->h_pinned[1], Sm1 = o->h_pinned[2];
+  moments[0] = S0;
+  moments[1] = S1;
+  moments[2] = Sm1;
+  moments[3] = S1 > 0 ? 6.283185307179586476925286766559 * S0 / S1 : NAN;
+  moments[4] = S0 > 0 ? Sm1 / S0 : NAN;
+  if (S_binned && nbins > 0) std::memcpy(S_binned, o->h_pinned + 3, nbins * sizeof(double));
+  return SHF_OK;
+}
+
+}  // namespace
+
+// =========================================================================
+extern "C" {
+
+int shf_version(void) { return kVersion; }
+
+const char* shf_strerror(int code) {
+  switch (code) {
+    case SHF_OK: return "ok";
+    case SHF_EINVAL: return "invalid argument";
+    case SHF_ENOMEM: return "out of memory";
+    case SHF_ECUDA: return "CUDA error";
+    case SHF_ENONFINITE: return "non-finite values in phi";
+    case SHF_ETIMEOUT: return "device wait timed out";
+    case SHF_EIO: return "checkpoint I/O error";
+    case SHF_ESTATE: return "invalid state for this call";
+    default: return "unknown error";
+  }
+}
+
+const char* shf_last_error(const shf_grid* g) { return g ? g->err.c_str() : "null grid"; }
+
+int shf_strain(int64_t n, double gdot, double dt, int nx, int ny, double* s, int64_t* wraps) {
+  if (!s || !wraps || !pow2_in_range(nx) || !pow2_in_range(ny) || nx % ny) return SHF_EINVAL;
+  long long K;
+  host_strain(n, gdot, dt, nx / ny, s, &K);
+  *wraps = K;
+  return SHF_OK;
+}
+
+int shf_noise_fill(double* out, int64_t count, uint64_t seed, double amp) {
+  if (!out || count < 0 || !std::isfinite(amp)) return SHF_EINVAL;
+  uint64_t state = seed;
+  for (int64_t k = 0; k < count; ++k) {
+    state += 0x9E3779B97F4A7C15ull;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    out[k] = amp * (2.0 * u - 1.0);
+  }
+  return SHF_OK;
+}
+
+int shf_create_grid(shf_grid** out, int nx, int ny, double dx, int precision, int remap_mode, void* cuda_stream) {
+  if (!out) return SHF_EINVAL;
+  *out = nullptr;
+  shf_grid tmp;
+  int rc = validate_size(&tmp, nx, ny, dx);
+  if (rc) return rc;
+  if (precision != SHF_FP32 && precision != SHF_FP64) return SHF_EINVAL;
+  if (remap_mode != SHF_REMAP_SHIFT && remap_mode != SHF_REMAP_NONE) return SHF_EINVAL;
+  shf_grid* g = new shf_grid();
+  g->kind = 0;
+  g->precision = precision;
+  g->remap_mode = remap_mode;
+  g->stream = static_cast<cudaStream_t>(cuda_stream);
+  rc = build(g, {nx}, {ny}, {dx});
+  if (rc) {
+    free_all(g);
+    return rc;
+  }
+  *out = g;
+  return SHF_OK;
+}
+
+int shf_create_ensemble(shf_grid** out, int nruns, const int* nx, const int* ny, const double* dx,
+                        const double* params, const uint64_t* seeds, double amp, int precision,
+                        void* cuda_stream) {
+  if (!out || nruns <= 0 || !nx || !ny || !params) return SHF_EINVAL;
+  *out = nullptr;
+  if (precision != SHF_FP32 && precision != SHF_FP64) return SHF_EINVAL;
+  shf_grid tmp;
+  std::vector<int> vx(nruns), vy(nruns);
+  std::vector<double> vd(nruns);
+  for (int r = 0; r < nruns; ++r) {
+    vx[r] = nx[r];
+    vy[r] = ny[r];
+    vd[r] = dx ? dx[r] : 1.0;
+    if (validate_size(&tmp, vx[r], vy[r], vd[r])) return SHF_EINVAL;
+    const double* p = params + 8 * r;
+    if (validate_params(&tmp, p[0], p[1], p[2], p[3], p[4], p[5], p[6], p[7])) return SHF_EINVAL;
+  }
+  shf_grid* g = new shf_grid();
+  g->kind = 1;
+  g->precision = precision;
+  g->remap_mode = SHF_REMAP_SHIFT;
+  g->stream = static_cast<cudaStream_t>(cuda_stream);
+  int rc = build(g, vx, vy, vd);
+  if (rc) {
+    free_all(g);
+    return rc;
+  }
+  for (int r = 0; r < nruns; ++r) {
+    Member& m = g->members[r];
+    const double* p = params + 8 * r;
+    m.a = p[0]; m.b = p[1]; m.kappa = p[2]; m.M = p[3]; m.eta = p[4]; m.rho = p[5]; m.gdot = p[6]; m.dt = p[7];
+    m.params_set = true;
+    rc = upload_desc(g, r);
+    if (rc) {
+      free_all(g);
+      return rc;
+    }
+  }
+  g->views.resize(nruns);
+  for (int r = 0; r < nruns; ++r) {
+    shf_grid* v = new shf_grid();
+    v->kind = 2;
+    v->parent = g;
+    v->member = r;
+    v->precision = precision;
+    v->device = g->device;
+    g->views[r] = v;
+  }
+  if (seeds) {
+    for (int r = 0; r < nruns; ++r) {
+      rc = shf_init_noise(g->views[r], seeds[r], amp);
+      if (rc) {
+        free_all(g);
+        return rc;
+      }
+    }
+  }
+  *out = g;
+  return SHF_OK;
+}
+
+int shf_ensemble_member(shf_grid* ens, int r, shf_grid** view) {
+  if (!ens || !view || ens->kind != 1 || r < 0 || r >= (int)ens->views.size()) return SHF_EINVAL;
+  *view = ens->views[r];
+  return SHF_OK;
+}
+
+int shf_destroy_grid(shf_grid* g) {
+  if (!g) return SHF_EINVAL;
+  if (g->kind == 2) return fail(g, SHF_EINVAL, "member views are freed with their ensemble");
+  free_all(g);
+  return SHF_OK;
+}
+
+int shf_set_params(shf_grid* g, double a, double b, double kappa, double M, double eta, double rho, double gdot,
+                   double dt) {
+  if (!g) return SHF_EINVAL;
+  int rc = validate_params(g, a, b, kappa, M, eta, rho, gdot, dt);
+  if (rc) return rc;
+  shf_grid* o = owner(g);
+  SHF_CUDA(g, cudaSetDevice(o->device));
+  std::vector<int> which;
+  if (g->kind == 1) {
+    for (size_t r = 0; r < o->members.size(); ++r) which.push_back((int)r);
+  } else {
+    which.push_back(member_index(g));
+  }
+  for (int r : which) {
+    Member& m = o->members[r];
+    m.a = a; m.b = b; m.kappa = kappa; m.M = M; m.eta = eta; m.rho = rho; m.gdot = gdot; m.dt = dt;
+    m.params_set = true;
+    rc = upload_desc(o, r);
+    if (rc) return fail(g, rc, o->err);
+  }
+  return SHF_OK;
+}
+
+
+int shf_set_fields(shf_grid* g, const double* phi, const double* psi, const double* omega) {
+  if (!g || !phi) return fail(g, SHF_EINVAL, "phi must not be NULL");
+  if (g->kind == 1) return fail(g, SHF_EINVAL, "use a member view to set fields of an ensemble");
+  SHF_CUDA(g, cudaSetDevice(owner(g)->device));
+  return g->precision == SHF_FP64 ? set_fields_t<double>(g, phi, psi, omega)
+                                  : set_fields_t<float>(g, phi, psi, omega);
+}
+
+int shf_init_noise(shf_grid* g, uint64_t seed, double amp) {
+  if (!g || !std::isfinite(amp)) return SHF_EINVAL;
+  if (g->kind == 1) return fail(g, SHF_EINVAL, "use a member view to initialise an ensemble member");
+  Member& m = *member_of(g);
+  std::vector<double> phi((size_t)m.nx * m.ny);
+  shf_noise_fill(phi.data(), (int64_t)phi.size(), seed, amp);
+  int rc = shf_set_fields(g, phi.data(), nullptr, nullptr);
+  if (rc) return rc;
+  if (g->kind == 0) return shf_set_step(g, 0);
+  return SHF_OK;
+}
+
+int shf_bind_device_fields(shf_grid* g, void* d_phi, void* d_psi, void* d_omega) {
+  if (!g || g->kind != 0 || !d_phi || !d_psi) return fail(g, SHF_EINVAL, "bind needs a grid and phi, psi");
+  Member& m = g->members[0];
+  const uintptr_t al = 15;
+  if (((uintptr_t)d_phi & al) || ((uintptr_t)d_psi & al) || (d_omega && ((uintptr_t)d_omega & al)))
+    return fail(g, SHF_EINVAL, "bound buffers must be 16-byte aligned");
+  if (!d_omega && m.rho > 0) return fail(g, SHF_EINVAL, "omega is needed for an inertial grid");
+  SHF_CUDA(g, cudaSetDevice(g->device));
+  const size_t bytes = (size_t)m.nx * m.ny * real_size(g);
+  SHF_CUDA(g, cudaMemcpyAsync(d_phi, m.phi, bytes, cudaMemcpyDeviceToDevice, g->stream));
+  SHF_CUDA(g, cudaMemcpyAsync(d_psi, m.psi, bytes, cudaMemcpyDeviceToDevice, g->stream));
+  if (d_omega) SHF_CUDA(g, cudaMemcpyAsync(d_omega, m.omega, bytes, cudaMemcpyDeviceToDevice, g->stream));
+  SHF_CUDA(g, cudaStreamSynchronize(g->stream));
+  if (!m.bound) {
+    cudaFree(m.phi);
+    cudaFree(m.psi);
+    if (d_omega) cudaFree(m.omega);
+  }
+  m.phi = d_phi;
+  m.psi = d_psi;
+  if (d_omega) m.omega = d_omega;
+  m.bound = true;
+  return upload_desc(g, 0);
+}
+
+int shf_set_step(shf_grid* g, int64_t n) {
+  if (!g || n < 0) return SHF_EINVAL;
+  if (g->kind == 2) return fail(g, SHF_EINVAL, "the step counter belongs to the ensemble");
+  SHF_CUDA(g, cudaSetDevice(g->device));
+  std::vector<long long> v(g->members.size(), (long long)n);
+  SHF_CUDA(g, cudaMemcpyAsync(g->d_counters, v.data(), v.size() * sizeof(long long), cudaMemcpyHostToDevice,
+                              g->stream));
+  SHF_CUDA(g, cudaStreamSynchronize(g->stream));
+  g->n = n;
+  return SHF_OK;
+}
+
+int shf_step(shf_grid* g, int64_t nsteps) {
+  if (!g || nsteps < 0) return SHF_EINVAL;
+  if (g->kind == 2) return fail(g, SHF_EINVAL, "step the ensemble, not a member view");
+  for (auto& m : g->members)
+    if (!m.params_set) return fail(g, SHF_ESTATE, "shf_set_params must be called before shf_step");
+  SHF_CUDA(g, cudaSetDevice(g->device));
+  long long left = nsteps;
+  if (left >= kGraphSteps) {
+    if (!g->graph) {
+      cudaGraph_t graph;
+      SHF_CUDA(g, cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+      enqueue_steps(g, kGraphSteps);
+      cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
+      if (e != cudaSuccess) return fail(g, SHF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&g->graph, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        g->graph = nullptr;
+        return fail(g, SHF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      }
+    }
+    while (left >= kGraphSteps) {
+      SHF_CUDA(g, cudaGraphLaunch(g->graph, g->stream));
+      left -= kGraphSteps;
+    }
+  }
+  enqueue_steps(g, left);
+  SHF_CUDA(g, cudaGetLastError());
+  g->n += nsteps;
+  return SHF_OK;
+}
+
+int shf_profile_step(shf_grid* g, int64_t nsteps, double* kernel_ms, int nkinds) {
+  if (!g || nsteps <= 0 || !kernel_ms || nkinds < kKinds) return fail(g, SHF_EINVAL, "bad profile arguments");
+  if (g->kind == 2) return fail(g, SHF_EINVAL, "step the ensemble, not a member view");
+  for (auto& m : g->members)
+    if (!m.params_set) return fail(g, SHF_ESTATE, "shf_set_params must be called before shf_profile_step");
+  SHF_CUDA(g, cudaSetDevice(g->device));
+  const size_t ncls = g->classes.size();
+  const size_t nev = (size_t)nsteps * ncls * (kKinds + 1);
+  std::vector<cudaEvent_t> ev(nev, nullptr);
+  int rc = SHF_OK;
+  for (size_t e = 0; e < nev && rc == SHF_OK; ++e)
+    if (cudaEventCreate(&ev[e]) != cudaSuccess) rc = fail(g, SHF_ECUDA, "event creation failed");
+  if (rc == SHF_OK) {
+    for (int64_t st = 0; st < nsteps; ++st) {
+      for (size_t c = 0; c < ncls; ++c) {
+        cudaEvent_t* e = &ev[((size_t)st * ncls + c) * (kKinds + 1)];
+        for (int k = 0; k < kKinds; ++k) {
+          cudaEventRecord(e[k], g->stream);
+          if (g->precision == SHF_FP64) launch_kind<double>(g, g->classes[c], k);
+          else launch_kind<float>(g, g->classes[c], k);
+        }
+        cudaEventRecord(e[kKinds], g->stream);
+      }
+    }
+    cudaError_t err = cudaGetLastError();
+    if (err == cudaSuccess) err = cudaStreamSynchronize(g->stream);
+    if (err != cudaSuccess) rc = fail(g, SHF_ECUDA, std::string("profiled step: ") + cudaGetErrorString(err));
+    g->n += nsteps;
+  }
+  if (rc == SHF_OK) {
+    for (int k = 0; k < nkinds; ++k) kernel_ms[k] = 0.0;
+    for (size_t b = 0; b < (size_t)nsteps * ncls; ++b) {
+      for (int k = 0; k < kKinds; ++k) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[b * (kKinds + 1) + k], ev[b * (kKinds + 1) + k + 1]);
+        kernel_ms[k] += ms;
+      }
+    }
+    for (int k = 0; k < kKinds; ++k) kernel_ms[k] /= (double)nsteps;
+  }
+  for (cudaEvent_t e : ev)
+    if (e) cudaEventDestroy(e);
+  return rc;
+}
+
+int shf_sync(shf_grid* g) {
+  if (!g) return SHF_EINVAL;
+  shf_grid* o = owner(g);
+  SHF_CUDA(g, cudaSetDevice(o->device));
+  SHF_CUDA(g, cudaStreamSynchronize(o->stream));
+  SHF_CUDA(g, cudaGetLastError());
+  std::vector<int> which;
+  if (g->kind == 1) {
+    for (size_t r = 0; r < o->members.size(); ++r) which.push_back((int)r);
+  } else {
+    which.push_back(member_index(g));
+  }
+  for (int r : which) {
+    double total, nf;
+    const Member& m = o->members[r];
+    int rc = o->precision == SHF_FP64 ? field_sum<double>(o, m, m.phi, &total, &nf)
+                                      : field_sum<float>(o, m, m.phi, &total, &nf);
+    if (rc) return fail(g, rc, o->err);
+    if (nf > 0) return fail(g, SHF_ENONFINITE, "phi holds non-finite values");
+  }
+  return SHF_OK;
+}
+
+
+int shf_get_fields(shf_grid* g, double* phi, double* psi, double* omega) {
+  if (!g) return SHF_EINVAL;
+  if (g->kind == 1) return fail(g, SHF_EINVAL, "use a member view to read fields of an ensemble");
+  SHF_CUDA(g, cudaSetDevice(owner(g)->device));
+  return g->precision == SHF_FP64 ? get_fields_t<double>(g, phi, psi, omega)
+                                  : get_fields_t<float>(g, phi, psi, omega);
+}
+
+int shf_get_time(shf_grid* g, int64_t* n, double* t, double* s, int64_t* wraps) {
+  if (!g) return SHF_EINVAL;
+  shf_grid* o = owner(g);
+  const Member& m = g->kind == 1 ? o->members[0] : *member_of(g);
+  double sv;
+  long long K;
+  host_strain(o->n, m.gdot, m.dt, m.nx / m.ny, &sv, &K);
+  if (n) *n = o->n;
+  if (t) *t = (double)o->n * m.dt;
+  if (s) *s = sv;
+  if (wraps) *wraps = K;
+  return SHF_OK;
+}
+
+int shf_mass(shf_grid* g, double* mean_phi) {
+  if (!g || !mean_phi) return SHF_EINVAL;
+  if (g->kind == 1) return fail(g, SHF_EINVAL, "use a member view for the mass of an ensemble member");
+  shf_grid* o = owner(g);
+  SHF_CUDA(g, cudaSetDevice(o->device));
+  const Member& m = *member_of(g);
+  double total, nf;
+  int rc = o->precision == SHF_FP64 ? field_sum<double>(o, m, m.phi, &total, &nf)
+                                    : field_sum<float>(o, m, m.phi, &total, &nf);
+  if (rc) return fail(g, rc, o->err);
+  *mean_phi = total / ((double)m.nx * (double)m.ny);
+  if (nf > 0) {
+    *mean_phi = NAN;
+    return fail(g, SHF_ENONFINITE, "phi holds non-finite values");
+  }
+  return SHF_OK;
+}
+
+
+int shf_structure_factor(shf_grid* g, double* S_binned, int nbins, double moments[5]) {
+  if (!g || !moments || nbins < 0 || nbins > 4096 || (nbins > 0 && !S_binned))
+    return fail(g, SHF_EINVAL, "bad structure factor arguments");
+  if (g->kind == 1) return fail(g, SHF_EINVAL, "use a member view for an ensemble member");
+  SHF_CUDA(g, cudaSetDevice(owner(g)->device));
+  return g->precision == SHF_FP64 ? sf_t<double>(g, S_binned, nbins, moments)
+                                  : sf_t<float>(g, S_binned, nbins, moments);
+}
+
+int shf_save(shf_grid* g, const char* path) {
+  if (!g || !path || g->kind != 0) return fail(g, SHF_EINVAL, "save needs a single grid and a path");
+  SHF_CUDA(g, cudaSetDevice(g->device));
+  const Member& m = g->members[0];
+  const size_t bytes = (size_t)m.nx * m.ny * real_size(g);
+  std::vector<unsigned char> payload(3 * bytes);
+  const void* src[3] = {m.phi, m.psi, m.omega};
+  for (int f = 0; f < 3; ++f)
+    SHF_CUDA(g, cudaMemcpyAsync(payload.data() + f * bytes, src[f], bytes, cudaMemcpyDeviceToHost, g->stream));
+  SHF_CUDA(g, cudaStreamSynchronize(g->stream));
+  CkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, "SHFCKPT1", 8);
+  h.version = 1;
+  h.nx = m.nx;
+  h.ny = m.ny;
+  h.precision = g->precision;
+  h.remap_mode = g->remap_mode;
+  h.has_params = m.params_set ? 1 : 0;
+  const double pv[9] = {m.a, m.b, m.kappa, m.M, m.eta, m.rho, m.gdot, m.dt, m.dx};
+  std::memcpy(h.params, pv, sizeof(pv));
+  h.n = g->n;
+  h.payload_crc = crc32_update(0, payload.data(), payload.size());
+  h.header_crc = crc32_update(0, reinterpret_cast<const unsigned char*>(&h), offsetof(CkptHeader, header_crc));
+  FILE* fp = std::fopen(path, "wb");
+  if (!fp) return fail(g, SHF_EIO, std::string("cannot open ") + path);
+  bool ok = std::fwrite(&h, sizeof(h), 1, fp) == 1 && std::fwrite(payload.data(), 1, payload.size(), fp) == payload.size();
+  ok = (std::fclose(fp) == 0) && ok;
+  if (!ok) return fail(g, SHF_EIO, "write failed");
+  return SHF_OK;
+}
+
+int shf_load(shf_grid* g, const char* path) {
+  if (!g || !path || g->kind != 0) return fail(g, SHF_EINVAL, "load needs a single grid and a path");
+  FILE* fp = std::fopen(path, "rb");
+  if (!fp) return fail(g, SHF_EIO, std::string("cannot open ") + path);
+  CkptHeader h;
+  const bool got = std::fread(&h, sizeof(h), 1, fp) == 1;
+  Member& m = g->members[0];
+  const size_t bytes = (size_t)m.nx * m.ny * real_size(g);
+  std::vector<unsigned char> payload(3 * bytes);
+  bool ok = got && std::memcmp(h.magic, "SHFCKPT1", 8) == 0 && h.version == 1 &&
+            h.header_crc == crc32_update(0, reinterpret_cast<const unsigned char*>(&h), offsetof(CkptHeader, header_crc));
+  if (ok && (h.nx != m.nx || h.ny != m.ny || h.precision != g->precision)) {
+    std::fclose(fp);
+    return fail(g, SHF_EINVAL, "checkpoint was written for another grid size or precision");
+  }
+  ok = ok && std::fread(payload.data(), 1, payload.size(), fp) == payload.size();
+  unsigned char extra;
+  ok = ok && std::fread(&extra, 1, 1, fp) == 0;
+  std::fclose(fp);
+  if (!ok || h.payload_crc != crc32_update(0, payload.data(), payload.size()))
+    return fail(g, SHF_EIO, "checkpoint truncated or corrupt");
+  SHF_CUDA(g, cudaSetDevice(g->device));
+  void* dst[3] = {m.phi, m.psi, m.omega};
+  for (int f = 0; f < 3; ++f)
+    SHF_CUDA(g, cudaMemcpyAsync(dst[f], payload.data() + f * bytes, bytes, cudaMemcpyHostToDevice, g->stream));
+  SHF_CUDA(g, cudaStreamSynchronize(g->stream));
+  g->remap_mode = h.remap_mode;
+  if (h.has_params) {
+    const double* p = h.params;
+    m.a = p[0]; m.b = p[1]; m.kappa = p[2]; m.M = p[3]; m.eta = p[4]; m.rho = p[5]; m.gdot = p[6]; m.dt = p[7];
+    m.params_set = true;
+  }
+  int rc = upload_desc(g, 0);
+  if (rc) return rc;
+  return shf_set_step(g, h.n);
+}
+
+}  // extern "C"

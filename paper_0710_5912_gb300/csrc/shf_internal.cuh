@@ -1,0 +1,96 @@
+// Internal declarations shared by the kernels and the host orchestration.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft_block.cuh"
+
+namespace shf {
+
+// Per-member descriptor, resident in device memory (one entry per run of a
+// batched launch; blockIdx.y selects the member).  All fields are row-major
+// ny x nx reals; the x-spectral ("row-transformed") buffers hold, per row j,
+// the modes m = 0 .. nx/2-1 of the row's real DFT (the Nyquist column
+// m = nx/2 is never stored: the scheme zeroes it).
+struct MemberDesc {
+  void* phi;
+  void* psi;
+  void* omega;
+  void* xs_phi;   // phi* -> phi^{n+1} (x-spectral)
+  void* xs_f;     // f = phi^3 (x-spectral)
+  void* xs_w;     // omega* -> omega^{n+1} (x-spectral)
+  void* xs_g;     // g = -F/rho or -F/eta -> psi^{n+1} (x-spectral)
+  long long* n;   // device step counter
+  // parameters and derived constants (double; cast to the working precision)
+  double a, b, kappa, M, eta, rho, gdot, dt, dx;
+  double c_dt_aM;        // dt a M
+  double c_dt_bM;        // dt b M
+  double c_hdt_kM;       // dt kappa M / 2
+  double c_hdt_nu;       // dt (eta / rho) / 2      (inertial)
+  double c_force;        // -1/rho (inertial) or -1/eta (Stokes), multiplies F
+  double inv_2h, inv_h2, inv_4h2;
+  double inv_nxny;       // 1 / (nx ny), the inverse-transform normalisation
+  double qx_unit, qy_unit;  // 2 pi / (nx dx), 2 pi / (ny dx)
+  int stokes;            // rho == 0
+  int remap;             // 1 when the SHIFT remap is active
+  int ratio;             // nx / ny
+  int pad_;
+};
+
+// Strain sawtooth of Section V from the integer step n (same operation order
+// as the host and the oracle; explicit rounding intrinsics keep the compiler
+// from contracting it): total = (gdot dt) n, K = floor(total / r + 1/2),
+// s = total - K r.
+__device__ __forceinline__ void strain_dev(long long n, double gdot, double dt, int r, double& s,
+                                           long long& K) {
+  const double total = __dmul_rn(__dmul_rn(gdot, dt), (double)n);
+  const double Kd = floor(__dadd_rn(__ddiv_rn(total, (double)r), 0.5));
+  s = __dsub_rn(total, __dmul_rn(Kd, (double)r));
+  K = (long long)Kd;
+}
+
+// ---- kernel launchers (step_kernels.cu / diag_kernels.cu) ----
+struct RowCfg {
+  int inst_per_cta;   // FFT instances per CTA
+  int threads;        // inst_per_cta * nx / 8
+  int ctas;           // grid.x
+  size_t smem;        // dynamic shared memory bytes
+};
+struct ColCfg {
+  int cols_per_cta;
+  int threads;        // cols_per_cta * ny / 8
+  int ctas;
+  size_t smem;
+};
+
+template <class T> void launch_stage1(const MemberDesc* d, int nmem, int log2nx, int log2ny,
+                                      const cplx<T>* tw, const RowCfg& c, cudaStream_t st);
+template <class T> void launch_colpass_phi(const MemberDesc* d, int nmem, int log2nx, int log2ny,
+                                           const cplx<T>* tw, const ColCfg& c, cudaStream_t st);
+// mode 0: phi rows pairs (x-spectral phi -> real phi, remap shift); mode 1:
+// final flow (psi,omega same row for inertial members, psi row pairs for Stokes)
+template <class T> void launch_rowinv(const MemberDesc* d, int nmem, int log2nx, int log2ny,
+                                      const cplx<T>* tw, const RowCfg& c, int mode, cudaStream_t st);
+template <class T> void launch_stage2(const MemberDesc* d, int nmem, int log2nx, int log2ny,
+                                      const cplx<T>* tw, const RowCfg& c, cudaStream_t st);
+template <class T> void launch_colpass_flow(const MemberDesc* d, int nmem, int log2nx, int log2ny,
+                                            const cplx<T>* tw, const ColCfg& c, cudaStream_t st);
+
+template <class T> void launch_convert_in(const double* src, T* dst, long long count, cudaStream_t st);
+template <class T> void launch_convert_out(const T* src, double* dst, long long count, cudaStream_t st);
+// partial Neumaier sums of a real field: out[3*b + {0,1,2}] = (sum, compensation,
+// non-finite count) of CTA b; returns the number of CTAs used
+template <class T> int launch_mass_partials(const T* f, long long count, double* out, int max_ctas,
+                                            cudaStream_t st);
+// structure factor: row transform of phi into xs (complex ny x nx/2), then per
+// CTA partial moments (sum S, sum kS, sum S/k) and per-CTA bins
+template <class T> void launch_sf_rows(const T* phi, cplx<T>* xs, int log2nx, int log2ny,
+                                       const cplx<T>* tw, const RowCfg& c, cudaStream_t st);
+template <class T> void launch_sf_cols(const cplx<T>* xs, int log2nx, int log2ny, double dx, double s,
+                                       const cplx<T>* tw, const ColCfg& c, double* partials, int nbins,
+                                       double* bin_partials, cudaStream_t st);
+void launch_reduce_rows(const double* in, int rows, int cols, double* out, cudaStream_t st);
+template <class T> void set_step_smem_limits();
+template <class T> void set_diag_smem_limits();
+
+}  // namespace shf
