@@ -62,13 +62,13 @@ const char* shf_strerror(int code);
 const char* shf_last_error(const shf_grid* g);
 
 /* Create a grid of nx by ny points with spacing dx (dx = dy), Appendix B's
- * (Lx N / Ly) x N mesh.  nx, ny: powers of two in [8, 4096] with ny dividing nx
+ * (Lx N / Ly) x N mesh.  nx, ny: powers of two in [16, 4096] with ny dividing nx
  * (the remap shifts row j by j*nx/ny cells).  precision: SHF_FP32 (bulk float
  * arithmetic; strain, sheared-wavenumber phase and mass in double) or SHF_FP64.
  * cuda_stream: a cudaStream_t to enqueue on, or NULL for a library-owned
  * stream.  The state starts at phi = psi = omega = 0, step 0; parameters must
- * be set before stepping.  Allocates about (3 + 4) * nx * ny * sizeof(real)
- * bytes of device memory. */
+ * be set before stepping.  Allocates about 9 * nx * ny * sizeof(real) bytes of
+ * device memory (state, phi* and omega*, four x-spectral work arrays). */
 int shf_create_grid(shf_grid** out, int nx, int ny, double dx, int precision, int remap_mode,
                     void* cuda_stream);
 

@@ -31,6 +31,9 @@ struct Member {
   void* omega = nullptr;
   bool bound = false;
   void* xs[4] = {nullptr, nullptr, nullptr, nullptr};
+  void* phi_star = nullptr;
+  void* omega_star = nullptr;
+  void* nyq = nullptr;        // 2 ny reals: nyq_phi then nyq_omega
   long long* d_n = nullptr;   // into the owner's counter array
   int cls = -1, slot = -1;
 };
@@ -49,7 +52,7 @@ int ilog2(int v) {
   while ((1 << l) < v) ++l;
   return l;
 }
-bool pow2_in_range(int v) { return v >= 8 && v <= NMAX && (v & (v - 1)) == 0; }
+bool pow2_in_range(int v) { return v >= 16 && v <= NMAX && (v & (v - 1)) == 0; }
 
 }  // namespace
 
@@ -66,7 +69,8 @@ struct shf_grid {
   std::vector<SizeClass> classes;
   long long* d_counters = nullptr;
   long long n = 0;
-  void* d_tw = nullptr;
+  void* d_tw = nullptr;     // W[k] = exp(2 pi i k / NMAX) (shared-memory FFTs of the diagnostics)
+  void* d_twr = nullptr;    // per-stage tables of the register FFT (step kernels)
   double* d_stage = nullptr;
   size_t stage_count = 0;
   double* d_scratch = nullptr;
@@ -119,7 +123,51 @@ void unit_root(long k, long N, double* c, double* s) {
   }
 }
 
-RowCfg row_cfg(int nx, int ny, int instances, size_t bytes_per_inst) {
+// Row kernels of the step: nx/16 threads per FFT instance (one pair of rows).
+RowCfg row_cfg(int nx, int ny, size_t bytes_per_inst) {
+  RowCfg c{};
+  const int Tf = nx / 16;
+  int ipc = 256 / Tf;
+  if (ipc < 1) ipc = 1;
+  if (ipc > ny / 2) ipc = ny / 2;
+  while (ipc > 1 && ipc * bytes_per_inst > kSmemLimit) ipc /= 2;
+  c.inst_per_cta = ipc;
+  c.threads = ipc * Tf;
+  c.ctas = (ny / 2) / ipc;
+  c.smem = ipc * bytes_per_inst;
+  return c;
+}
+
+// Persistent row kernels walk row pairs with a grid stride: at most
+// ctas_per_sm CTAs per SM (their register-limited residency).
+RowCfg persistent(RowCfg c, int ctas_per_sm) {
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 1;
+  if (c.ctas > sms * ctas_per_sm) c.ctas = sms * ctas_per_sm;
+  return c;
+}
+
+// Column kernels of the step: ny/16 threads per column, NC columns per CTA,
+// NC a multiple of the layout's chunk width.
+ColCfg col_cfg(int nx, int ny, int chunk, size_t bytes_per_col, int max_threads) {
+  ColCfg c{};
+  const int Tc = ny / 16;
+  int C = 256 / Tc;
+  if (C < chunk) C = chunk;
+  if (C > nx / 2) C = nx / 2;
+  while (C > chunk && ((size_t)C * bytes_per_col > kSmemLimit || C * Tc > max_threads)) C /= 2;
+  c.cols_per_cta = C;
+  c.log2cols = ilog2(C);
+  c.threads = C * Tc;
+  c.ctas = (nx / 2) / C;
+  c.smem = (size_t)C * bytes_per_col;
+  return c;
+}
+
+// Diagnostic (structure factor) kernels: nx/8 or ny/8 threads per FFT.
+RowCfg sf_row_cfg(int nx, int ny, size_t bytes_per_inst) {
   RowCfg c{};
   const int Tf = nx / 8;
   int ipc = 256 / Tf;
@@ -128,12 +176,12 @@ RowCfg row_cfg(int nx, int ny, int instances, size_t bytes_per_inst) {
   while (ipc > 1 && ipc * bytes_per_inst > kSmemLimit) ipc /= 2;
   c.inst_per_cta = ipc;
   c.threads = ipc * Tf;
-  c.ctas = (instances + ipc - 1) / ipc;
+  c.ctas = (ny / 2) / ipc;
   c.smem = ipc * bytes_per_inst;
   return c;
 }
 
-ColCfg col_cfg(int nx, int ny, size_t bytes_per_row_per_col, size_t elem, int max_threads) {
+ColCfg sf_col_cfg(int nx, int ny, size_t bytes_per_row_per_col, size_t elem) {
   ColCfg c{};
   const int Tc = ny / 8;
   int cmin = (int)(32 / elem);
@@ -141,8 +189,9 @@ ColCfg col_cfg(int nx, int ny, size_t bytes_per_row_per_col, size_t elem, int ma
   int C = 256 / Tc;
   if (C < cmin) C = cmin;
   if (C > nx / 2) C = nx / 2;
-  while (C > 1 && ((size_t)C * ny * bytes_per_row_per_col > kSmemLimit || C * Tc > max_threads)) C /= 2;
+  while (C > 1 && ((size_t)C * ny * bytes_per_row_per_col > kSmemLimit || C * Tc > 512)) C /= 2;
   c.cols_per_cta = C;
+  c.log2cols = ilog2(C);
   c.threads = C * Tc;
   c.ctas = (nx / 2) / C;
   c.smem = (size_t)C * ny * bytes_per_row_per_col;
@@ -152,16 +201,18 @@ ColCfg col_cfg(int nx, int ny, size_t bytes_per_row_per_col, size_t elem, int ma
 void configure_class(SizeClass& cl, int precision) {
   const size_t R = precision == SHF_FP64 ? 8 : 4;   // real
   const size_t Cx = 2 * R;                            // complex
+  const int chunk = precision == SHF_FP64 ? 1 : 2;    // x-spectral tile width (16 bytes)
   const int nx = cl.nx, ny = cl.ny;
-  cl.stage1 = row_cfg(nx, ny, ny / 2, 3 * nx * Cx);
-  cl.rowinv0 = row_cfg(nx, ny, ny / 2, nx * Cx);
-  cl.rowinv1 = row_cfg(nx, ny, ny, nx * Cx);
-  cl.stage2 = row_cfg(nx, ny, ny / 2, nx * (Cx + 4 * R));
-  cl.sfrows = row_cfg(nx, ny, ny / 2, nx * Cx);
-  const int colmax = precision == SHF_FP64 ? 512 : 1024;   // matches the kernels' launch bounds
-  cl.colphi = col_cfg(nx, ny, 2 * Cx, Cx, colmax);
-  cl.colflow = col_cfg(nx, ny, 2 * Cx, Cx, colmax);
-  cl.sfcols = col_cfg(nx, ny, Cx + 12, Cx, 512);
+  const size_t prow = (size_t)padded_len(nx) * Cx, pcol = (size_t)padded_len(ny) * Cx;
+  cl.stage1 = row_cfg(nx, ny, stage1_inst_bytes(nx, R));
+  cl.rowinv0 = persistent(row_cfg(nx, ny, prow), 2);
+  cl.rowinv1 = row_cfg(nx, ny, prow);
+  cl.stage2 = row_cfg(nx, ny, stage2_inst_bytes(nx, R));
+  const int colmax = precision == SHF_FP64 ? 256 : 512;   // the column kernels' launch bounds
+  cl.colphi = col_cfg(nx, ny, chunk, pcol, colmax);
+  cl.colflow = col_cfg(nx, ny, chunk, pcol, colmax);
+  cl.sfrows = sf_row_cfg(nx, ny, nx * Cx);
+  cl.sfcols = sf_col_cfg(nx, ny, Cx + 12, Cx);
 }
 
 void host_strain(long long n, double gdot, double dt, int r, double* s, long long* K) {
@@ -182,6 +233,10 @@ MemberDesc make_desc(const shf_grid* o, const Member& m) {
   d.xs_f = m.xs[1];
   d.xs_w = m.xs[2];
   d.xs_g = m.xs[3];
+  d.phi_star = m.phi_star;
+  d.omega_star = m.omega_star;
+  d.nyq_phi = m.nyq;
+  d.nyq_omega = static_cast<char*>(m.nyq) + (size_t)m.ny * (o->precision == SHF_FP64 ? 8 : 4);
   d.n = m.d_n;
   d.a = m.a; d.b = m.b; d.kappa = m.kappa; d.M = m.M; d.eta = m.eta; d.rho = m.rho;
   d.gdot = m.gdot; d.dt = m.dt; d.dx = m.dx;
@@ -259,10 +314,14 @@ void free_all(shf_grid* g) {
       cudaFree(m.omega);
     }
     for (void* p : m.xs) cudaFree(p);
+    cudaFree(m.phi_star);
+    cudaFree(m.omega_star);
+    cudaFree(m.nyq);
   }
   for (auto& cl : g->classes) cudaFree(cl.d_desc);
   cudaFree(g->d_counters);
   cudaFree(g->d_tw);
+  cudaFree(g->d_twr);
   cudaFree(g->d_stage);
   cudaFree(g->d_scratch);
   if (g->h_pinned) cudaFreeHost(g->h_pinned);
@@ -273,7 +332,7 @@ void free_all(shf_grid* g) {
 
 int validate_size(shf_grid* g, int nx, int ny, double dx) {
   if (!pow2_in_range(nx) || !pow2_in_range(ny))
-    return fail(g, SHF_EINVAL, "nx and ny must be powers of two in [8, 4096]");
+    return fail(g, SHF_EINVAL, "nx and ny must be powers of two in [16, 4096]");
   if (nx % ny != 0) return fail(g, SHF_EINVAL, "ny must divide nx");
   if (!(dx > 0.0) || !std::isfinite(dx)) return fail(g, SHF_EINVAL, "dx must be positive and finite");
   return SHF_OK;
@@ -320,11 +379,15 @@ int build(shf_grid* g, const std::vector<int>& nx, const std::vector<int>& ny, c
     m.dx = dx[r];
     m.d_n = g->d_counters + r;
     const size_t bytes = (size_t)m.nx * m.ny * R;
-    void** bufs[7] = {&m.phi, &m.psi, &m.omega, &m.xs[0], &m.xs[1], &m.xs[2], &m.xs[3]};
+    void** bufs[9] = {&m.phi, &m.psi, &m.omega, &m.xs[0], &m.xs[1], &m.xs[2], &m.xs[3], &m.phi_star,
+                      &m.omega_star};
     for (void** p : bufs) {
       if (cudaMalloc(p, bytes) != cudaSuccess) return fail(g, SHF_ENOMEM, "field allocation failed");
       SHF_CUDA(g, cudaMemsetAsync(*p, 0, bytes, g->stream));
     }
+    if (cudaMalloc(&m.nyq, 2 * (size_t)m.ny * R) != cudaSuccess)
+      return fail(g, SHF_ENOMEM, "field allocation failed");
+    SHF_CUDA(g, cudaMemsetAsync(m.nyq, 0, 2 * (size_t)m.ny * R, g->stream));
     int found = -1;
     for (size_t c = 0; c < g->classes.size(); ++c)
       if (g->classes[c].nx == m.nx && g->classes[c].ny == m.ny) found = (int)c;
@@ -351,18 +414,38 @@ int build(shf_grid* g, const std::vector<int>& nx, const std::vector<int>& ny, c
     int rc = upload_desc(g, r);
     if (rc) return rc;
   }
-  // twiddle table W[k] = exp(2 pi i k / NMAX) in the working precision
+  // twiddle table W[k] = exp(2 pi i k / NMAX) and the register FFT's stage
+  // tables (entry (log2Ns, LR, k, r) = exp(2 pi i k r / (Ns R))), both computed
+  // in double and rounded once to the working precision
   std::vector<double> tw(2 * NMAX);
   for (int k = 0; k < NMAX; ++k) unit_root(k, NMAX, &tw[2 * k], &tw[2 * k + 1]);
-  if (g->precision == SHF_FP64) {
-    if (cudaMalloc(&g->d_tw, NMAX * sizeof(double2)) != cudaSuccess) return fail(g, SHF_ENOMEM, "twiddles");
-    SHF_CUDA(g, cudaMemcpy(g->d_tw, tw.data(), NMAX * sizeof(double2), cudaMemcpyHostToDevice));
-  } else {
-    std::vector<float> twf(2 * NMAX);
-    for (int k = 0; k < 2 * NMAX; ++k) twf[k] = (float)tw[k];
-    if (cudaMalloc(&g->d_tw, NMAX * sizeof(float2)) != cudaSuccess) return fail(g, SHF_ENOMEM, "twiddles");
-    SHF_CUDA(g, cudaMemcpy(g->d_tw, twf.data(), NMAX * sizeof(float2), cudaMemcpyHostToDevice));
-  }
+  std::vector<double> twr(2 * (size_t)stage_table_len());
+  for (int a : {4, 8})
+    for (int lr = 1; lr <= 4; ++lr) {
+      const long Ns = 1L << a, R = 1L << lr, L = Ns * R;
+      for (long k = 0; k < Ns; ++k)
+        for (long r = 0; r < R; ++r) {
+          const size_t e = (size_t)stage_table_offset(a, lr) + k * R + r;
+          unit_root((k * r) % L, L, &twr[2 * e], &twr[2 * e + 1]);
+        }
+    }
+  auto upload = [&](void** dst, const std::vector<double>& src) -> int {
+    const size_t cnt = src.size() / 2;
+    if (g->precision == SHF_FP64) {
+      if (cudaMalloc(dst, cnt * sizeof(double2)) != cudaSuccess) return fail(g, SHF_ENOMEM, "twiddles");
+      SHF_CUDA(g, cudaMemcpy(*dst, src.data(), cnt * sizeof(double2), cudaMemcpyHostToDevice));
+    } else {
+      std::vector<float> f(src.size());
+      for (size_t i = 0; i < src.size(); ++i) f[i] = (float)src[i];
+      if (cudaMalloc(dst, cnt * sizeof(float2)) != cudaSuccess) return fail(g, SHF_ENOMEM, "twiddles");
+      SHF_CUDA(g, cudaMemcpy(*dst, f.data(), cnt * sizeof(float2), cudaMemcpyHostToDevice));
+    }
+    return SHF_OK;
+  };
+  int rc2 = upload(&g->d_tw, tw);
+  if (rc2) return rc2;
+  rc2 = upload(&g->d_twr, twr);
+  if (rc2) return rc2;
   SHF_CUDA(g, cudaStreamSynchronize(g->stream));
   return SHF_OK;
 }
@@ -370,7 +453,7 @@ int build(shf_grid* g, const std::vector<int>& nx, const std::vector<int>& ny, c
 // The six launches of one step for one size class, in order (kind 0..5).
 template <class T>
 void launch_kind(shf_grid* o, SizeClass& cl, int kind) {
-  const cplx<T>* tw = static_cast<const cplx<T>*>(o->d_tw);
+  const cplx<T>* tw = static_cast<const cplx<T>*>(o->d_twr);
   const int nm = (int)cl.members.size();
   switch (kind) {
     case 0: launch_stage1<T>(cl.d_desc, nm, cl.log2nx, cl.log2ny, tw, cl.stage1, o->stream); break;

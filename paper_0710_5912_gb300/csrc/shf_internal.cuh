@@ -10,8 +10,9 @@ namespace shf {
 // Per-member descriptor, resident in device memory (one entry per run of a
 // batched launch; blockIdx.y selects the member).  All fields are row-major
 // ny x nx reals; the x-spectral ("row-transformed") buffers hold, per row j,
-// the modes m = 0 .. nx/2-1 of the row's real DFT (the Nyquist column
-// m = nx/2 is never stored: the scheme zeroes it).
+// the modes m = 0 .. nx/2-1 of the row's real DFT in a tiled order (see
+// step_kernels.cu); the Nyquist column m = nx/2 is zeroed by the scheme and
+// only the row coefficient of phi* / omega* is kept, to subtract it.
 struct MemberDesc {
   void* phi;
   void* psi;
@@ -20,6 +21,10 @@ struct MemberDesc {
   void* xs_f;     // f = phi^3 (x-spectral)
   void* xs_w;     // omega* -> omega^{n+1} (x-spectral)
   void* xs_g;     // g = -F/rho or -F/eta -> psi^{n+1} (x-spectral)
+  void* phi_star;    // phi* = phi^n - dt J(psi, phi) (real), base of the increment
+  void* omega_star;  // omega* (real, already remapped at a wrap)
+  void* nyq_phi;     // per row: the real Nyquist coefficient of phi*'s row DFT
+  void* nyq_omega;   // per row: the same for omega*
   long long* n;   // device step counter
   // parameters and derived constants (double; cast to the working precision)
   double a, b, kappa, M, eta, rho, gdot, dt, dx;
@@ -49,6 +54,18 @@ __device__ __forceinline__ void strain_dev(long long n, double gdot, double dt, 
   K = (long long)Kd;
 }
 
+// Shared memory of one row-pair instance of the stage kernels (real_bytes =
+// sizeof(T)): stage 1 holds the padded FFT buffer plus two cp.async tiles of
+// 2 fields x 4 rows x (nx/16 + 4); stage 2 the buffer plus two phi tiles of
+// 6 rows x (nx/16 + 6) and a mu tile of 4 rows x (nx/16 + 4).
+__host__ __device__ constexpr size_t stage1_inst_bytes(int nx, size_t real_bytes) {
+  return (size_t)padded_len(nx) * 2 * real_bytes + 2 * 2 * 4 * (size_t)(nx / 16 + 4) * real_bytes;
+}
+__host__ __device__ constexpr size_t stage2_inst_bytes(int nx, size_t real_bytes) {
+  return (size_t)padded_len(nx) * 2 * real_bytes +
+         (2 * 6 * (size_t)(nx / 16 + 6) + 4 * (size_t)(nx / 16 + 4)) * real_bytes;
+}
+
 // ---- kernel launchers (step_kernels.cu / diag_kernels.cu) ----
 struct RowCfg {
   int inst_per_cta;   // FFT instances per CTA
@@ -58,6 +75,7 @@ struct RowCfg {
 };
 struct ColCfg {
   int cols_per_cta;
+  int log2cols;
   int threads;        // cols_per_cta * ny / 8
   int ctas;
   size_t smem;
