@@ -5,7 +5,7 @@ Workload: a 4096 x 4096 inertial run in FP32 (rho = eta = 1, a = b = kappa = M =
 dx = 1, gdot = 0.001, dt = 0.005) from the seeded +-0.01 quench, the large single
 run on which the metric (grid-point updates/s, FP32 against the same GPU's FP64
 path, and the fraction of the HBM roofline) is quoted.  A step is one full time
-step (six kernel launches).  The state plus scratch (448 MiB) exceeds L2, so no
+step (eight kernel launches).  The state plus scratch (448 MiB) exceeds L2, so no
 flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
@@ -42,12 +42,14 @@ FALLBACK_HBM_GBS = 6800.0
 # (4 B in FP32): fields read + fields written (an x-spectral field of nx/2
 # complex per row is one real per point)
 KERNEL_REALS_PER_POINT = {
-    "stage1_stencil_rowfft": 6,   # phi, psi, omega in; phi*, f, omega* (x-spectral) out
-    "colpass_phi": 3,             # phi*, f in; phi^{n+1} out
-    "rowinv_phi": 2,              # x-spectral phi in; real phi out
-    "stage2_stencil_rowfft": 2,   # phi in; g (x-spectral) out
-    "colpass_flow": 4,            # g, omega* in; psi, omega out
-    "rowinv_flow": 4,             # psi, omega (x-spectral) in; real psi, omega out
+    "stencil1": 5,        # phi, psi, omega in; phi*, omega* out
+    "rowfwd_phi": 6,      # phi*, phi, omega* in; phi*, f, omega* (x-spectral) out
+    "colpass_phi": 3,     # phi*, f in; phi increment out
+    "rowinv_phi": 3,      # increment, phi* in; phi out
+    "stencil2": 2,        # phi in; g out
+    "rowfwd_g": 2,        # g in; g (x-spectral) out
+    "colpass_flow": 4,    # g, omega* in; psi, omega increment out
+    "rowinv_flow": 5,     # psi, omega increment, omega* in; psi, omega out
 }
 KERNEL_SOURCES = ["paper_0710_5912_gb300/csrc/step_kernels.cu", "paper_0710_5912_gb300/csrc/fft_block.cuh",
                   "paper_0710_5912_gb300/csrc/shf_internal.cuh"]
@@ -360,7 +362,7 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "single grid",
                            "l2": "state + scratch 448 MiB > L2: inputs larger than L2, no flush"},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e,
-                "gpu_launches": 6 * args.steps,
+                "gpu_launches": len(KERNEL_REALS_PER_POINT) * args.steps,
                 "graph_ms_per_step": graph_ms_per_step,
                 "step_algorithmic_bytes": step_bytes,
                 "step_hbm_frac": step_bytes / (ms_per_step * 1e-3) / 1e9 / peak,

@@ -114,11 +114,12 @@ int shf_step(shf_grid* g, int64_t nsteps);
 
 /* Advance nsteps >= 1 steps like shf_step, but launch every kernel directly
  * with a CUDA event recorded on the grid's stream before and after it, and
- * return in kernel_ms[0..5] the mean device time per step of each of the six
- * launches of a step (stage-1 stencil + row transform, phi column pass, phi
- * row inverse, stage-2 stencil + row transform, flow column pass, flow row
- * inverse), summed over size classes.  nkinds must be >= 6.  Synchronising;
- * meant for measurement (per-kernel roofline), not for production runs. */
+ * return in kernel_ms[0..7] the mean device time per step of each of the eight
+ * launches of a step (stage-1 stencil, phi row transforms, phi column pass,
+ * phi row inverse, stage-2 stencil, g row transform, flow column pass, flow
+ * row inverse), summed over size classes.  nkinds must be >= 8.
+ * Synchronising; meant for measurement (per-kernel roofline), not for
+ * production runs. */
 int shf_profile_step(shf_grid* g, int64_t nsteps, double* kernel_ms, int nkinds);
 
 /* Wait for queued work; returns SHF_ENONFINITE if phi holds NaN/Inf. */

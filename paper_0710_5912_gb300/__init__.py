@@ -122,7 +122,7 @@ def shf_step(h, nsteps=1):
     _check(lib().shf_step(h, int(nsteps)), h, "shf_step")
 
 
-KERNEL_KINDS = ("stage1_stencil_rowfft", "colpass_phi", "rowinv_phi", "stage2_stencil_rowfft",
+KERNEL_KINDS = ("stencil1", "rowfwd_phi", "colpass_phi", "rowinv_phi", "stencil2", "rowfwd_g",
                 "colpass_flow", "rowinv_flow")
 
 

@@ -162,73 +162,40 @@ __device__ void fft_smem(C* const (&buf)[NB], int log2N, int tid, const C* __res
 }
 
 // ---------------------------------------------------------------------------
-// Register-resident FFT (16 points per thread).
+// Register-resident FFT (P = 8 points per thread).
 //
-// Thread t of an instance (0 <= t < T = N/16) holds v[q] = x[t + T q],
-// q = 0..15.  Each Stockham stage is radix 16 except possibly the last
-// (radix 8, 4 or 2 when log2 N is not a multiple of 4).  A stage's butterflies
-// j = t + b T (b < 16/R) read x[j + r N/R] = v[b + r 16/R] -- exactly the
+// Thread t of an instance (0 <= t < T = N/P) holds v[q] = x[t + T q],
+// q = 0..P-1.  Each Stockham stage is radix P except possibly the last (radix
+// 4 or 2 when log2 N is not a multiple of log2 P).  A stage's butterflies
+// j = t + b T (b < P/R) read x[j + r N/R] = v[b + r P/R] -- exactly the
 // register layout -- so the first stage needs no exchange, and the last
 // stage's outputs (positions j + r N/R) land in that same layout, so the
 // transform ends in registers with v[q] = X[t + T q].  Only the stages in
 // between exchange through shared memory.  Exchange buffers are padded by one
-// element per 16 (index i -> i + i/16) so that the radix-16 scatter of the
-// first stage is free of bank conflicts.
+// element per 16 (index i -> i + i/16), which keeps the scatter of the early
+// stages free of bank conflicts.  Eight points per thread (more threads, more
+// resident warps) measured faster on GB300 than sixteen with one stage less.
+constexpr int kP = 8;
+constexpr int kLogP = 3;
 
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
-
-// Per-stage twiddle tables of the register FFT.  A stage of radix R = 2^LR
-// after sub-transforms of length Ns = 2^log2Ns (log2Ns = 4 or 8; the first
-// stage, Ns = 1, needs none) multiplies input r of butterfly k = j mod Ns by
-// W_L^{k r}, L = Ns R.  The table stores exp(+2 pi i k r / L) at
-// [offset(log2Ns, LR) + k R + r], r = 0..R-1, so a thread reads its R factors
-// as contiguous 16-byte vectors and a warp reads contiguous rows.
-__host__ __device__ constexpr int stage_table_offset(int log2Ns, int LR) {
-  // blocks in the order (4,1),(4,2),(4,3),(4,4),(8,1),(8,2),(8,3),(8,4)
-  return (log2Ns == 4 ? 0 : 16 * (2 + 4 + 8 + 16)) + (1 << log2Ns) * ((1 << LR) - 2);
-}
-__host__ __device__ constexpr int stage_table_len() { return 16 * 30 + 256 * 30; }
 // elements of a padded exchange buffer for an N-point transform
 __host__ __device__ constexpr int padded_len(int N) { return N + N / 16; }
 
-// radix-16 DFT in place as 4 x 4: DFT4 over b of v[a + 4b], twiddle by
-// w16^{a c}, DFT4 over a; output X[c + 4d] sits at position 4c + d and is put
-// back in natural order at the end.
-template <bool INV, class C>
-__device__ __forceinline__ void dft16(C* v) {
-  using T = decltype(v[0].x);
-  const T c1 = T(0.92387953251128675612818318939678829);  // cos(pi/8)
-  const T s1 = T(0.38268343236508977172845998403039887);  // sin(pi/8)
-  const T h = T(0.70710678118654752440084436210484904);   // 1/sqrt(2)
-  const T sg = INV ? T(1) : T(-1);
-#pragma unroll
-  for (int a = 0; a < 4; ++a) dft4<INV>(v[a], v[a + 4], v[a + 8], v[a + 12]);
-  // v[a + 4c] *= w16^{a c}, w16 = exp(sigma 2 pi i / 16)
-  auto rot = [&](C x, T cr, T si) { return C{x.x * cr - sg * si * x.y, x.y * cr + sg * si * x.x}; };
-  v[1 + 4] = rot(v[1 + 4], c1, s1);     // a=1 c=1: w^1
-  v[1 + 8] = rot(v[1 + 8], h, h);       // a=1 c=2: w^2
-  v[1 + 12] = rot(v[1 + 12], s1, c1);   // a=1 c=3: w^3
-  v[2 + 4] = rot(v[2 + 4], h, h);       // a=2 c=1: w^2
-  v[2 + 8] = mul_si<INV>(v[2 + 8]);     // a=2 c=2: w^4 = sigma i
-  v[2 + 12] = rot(v[2 + 12], -h, h);    // a=2 c=3: w^6
-  v[3 + 4] = rot(v[3 + 4], s1, c1);     // a=3 c=1: w^3
-  v[3 + 8] = rot(v[3 + 8], -h, h);      // a=3 c=2: w^6
-  v[3 + 12] = rot(v[3 + 12], -c1, -s1); // a=3 c=3: w^9
-#pragma unroll
-  for (int c = 0; c < 4; ++c) dft4<INV>(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
-  C o[16];
-#pragma unroll
-  for (int c = 0; c < 4; ++c)
-#pragma unroll
-    for (int d = 0; d < 4; ++d) o[c + 4 * d] = v[4 * c + d];
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = o[i];
+// Per-stage twiddle tables.  A stage of radix R = 2^LR after sub-transforms of
+// length Ns = 2^a multiplies input r of butterfly k = j mod Ns by W_L^{k r},
+// L = Ns R.  The table stores exp(+2 pi i k r / L) at
+// [stage_table_offset(a, LR) + k R + r], r = 0..R-1, so a thread reads its R
+// factors as contiguous 16-byte vectors and a warp reads contiguous rows.
+// Blocks for a = 1..11, LR = 1..4 (only those with a + LR <= 12 are used).
+__host__ __device__ constexpr int stage_table_offset(int a, int LR) {
+  return 30 * ((1 << a) - 2) + (1 << a) * ((1 << LR) - 2);
 }
+__host__ __device__ constexpr int stage_table_len() { return 30 * ((1 << 12) - 2); }
 
 template <bool INV, int LR, class C>
 __device__ __forceinline__ void dft_radix(C* v) {
-  if (LR == 4) dft16<INV>(v);
-  else if (LR == 3) dft8<INV>(v);
+  if (LR == 3) dft8<INV>(v);
   else if (LR == 2) dft4<INV>(v[0], v[1], v[2], v[3]);
   else dft2<INV>(v[0], v[1]);
 }
@@ -237,11 +204,11 @@ __device__ __forceinline__ void dft_radix(C* v) {
 // otherwise scatter them to buf (padded), barrier, gather the next stage's
 // inputs, barrier (so the buffer can be written again).
 template <bool INV, int LR, bool LAST, class C>
-__device__ __forceinline__ void fft_reg_stage(C (&v)[16], int log2N, int log2Ns, int t, C* buf,
+__device__ __forceinline__ void fft_reg_stage(C (&v)[kP], int log2N, int log2Ns, int t, C* buf,
                                               const C* __restrict__ twt) {
   constexpr int R = 1 << LR;
-  constexpr int B = 16 >> LR;
-  const int T = 1 << (log2N - 4);
+  constexpr int B = kP >> LR;
+  const int T = 1 << (log2N - kLogP);
   const int Ns = 1 << log2Ns;
   C w[R];
 #pragma unroll
@@ -251,10 +218,10 @@ __device__ __forceinline__ void fft_reg_stage(C (&v)[16], int log2N, int log2Ns,
 #pragma unroll
     for (int r = 0; r < R; ++r) w[r] = v[b + r * B];
     if (log2Ns > 0) {
-      // R factors of this butterfly: one contiguous row of the stage table
+      // the R factors of this butterfly: one contiguous row of the stage table
       const C* row = twt + stage_table_offset(log2Ns, LR) + k * R;
       C f[R];
-      if (sizeof(C) == 8 && R >= 2) {
+      if (sizeof(C) == 8) {
         const float4* r4 = reinterpret_cast<const float4*>(row);
 #pragma unroll
         for (int h = 0; h < R / 2; ++h) {
@@ -282,7 +249,7 @@ __device__ __forceinline__ void fft_reg_stage(C (&v)[16], int log2N, int log2Ns,
   if (!LAST) {
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = buf[pad16(t + q * T)];
+    for (int q = 0; q < kP; ++q) v[q] = buf[pad16(t + q * T)];
     __syncthreads();
   }
 }
@@ -292,14 +259,13 @@ __device__ __forceinline__ void fft_reg_stage(C (&v)[16], int log2N, int log2Ns,
 // the stage tables (stage_table_offset).  All threads of the CTA must call it
 // (barriers) with the same log2N.
 template <bool INV, class C>
-__device__ __forceinline__ void fft_reg(C (&v)[16], int log2N, int t, C* buf, const C* __restrict__ tw) {
+__device__ __forceinline__ void fft_reg(C (&v)[kP], int log2N, int t, C* buf, const C* __restrict__ tw) {
   int log2Ns = 0;
-  while (log2N - log2Ns > 4) {
-    fft_reg_stage<INV, 4, false>(v, log2N, log2Ns, t, buf, tw);
-    log2Ns += 4;
+  while (log2N - log2Ns > kLogP) {
+    fft_reg_stage<INV, kLogP, false>(v, log2N, log2Ns, t, buf, tw);
+    log2Ns += kLogP;
   }
   switch (log2N - log2Ns) {
-    case 4: fft_reg_stage<INV, 4, true>(v, log2N, log2Ns, t, buf, tw); break;
     case 3: fft_reg_stage<INV, 3, true>(v, log2N, log2Ns, t, buf, tw); break;
     case 2: fft_reg_stage<INV, 2, true>(v, log2N, log2Ns, t, buf, tw); break;
     default: fft_reg_stage<INV, 1, true>(v, log2N, log2Ns, t, buf, tw); break;
@@ -308,10 +274,10 @@ __device__ __forceinline__ void fft_reg(C (&v)[16], int log2N, int t, C* buf, co
 
 // v[q] = X[t + T q] -> buf (padded, natural order), followed by a barrier.
 template <class C>
-__device__ __forceinline__ void reg_to_smem(const C (&v)[16], int log2N, int t, C* buf) {
-  const int T = 1 << (log2N - 4);
+__device__ __forceinline__ void reg_to_smem(const C (&v)[kP], int log2N, int t, C* buf) {
+  const int T = 1 << (log2N - kLogP);
 #pragma unroll
-  for (int q = 0; q < 16; ++q) buf[pad16(t + q * T)] = v[q];
+  for (int q = 0; q < kP; ++q) buf[pad16(t + q * T)] = v[q];
   __syncthreads();
 }
 

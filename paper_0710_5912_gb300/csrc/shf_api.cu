@@ -43,8 +43,9 @@ struct SizeClass {
   std::vector<int> members;
   std::vector<MemberDesc> h_desc;
   MemberDesc* d_desc = nullptr;
-  RowCfg stage1{}, rowinv0{}, rowinv1{}, stage2{}, sfrows{};
-  ColCfg colphi{}, colflow{}, sfcols{};
+  LaunchCfg cfg[KIND_COUNT]{};
+  RowCfg sfrows{};
+  ColCfg sfcols{};
 };
 
 int ilog2(int v) {
@@ -123,49 +124,6 @@ void unit_root(long k, long N, double* c, double* s) {
   }
 }
 
-// Row kernels of the step: nx/16 threads per FFT instance (one pair of rows).
-RowCfg row_cfg(int nx, int ny, size_t bytes_per_inst) {
-  RowCfg c{};
-  const int Tf = nx / 16;
-  int ipc = 256 / Tf;
-  if (ipc < 1) ipc = 1;
-  if (ipc > ny / 2) ipc = ny / 2;
-  while (ipc > 1 && ipc * bytes_per_inst > kSmemLimit) ipc /= 2;
-  c.inst_per_cta = ipc;
-  c.threads = ipc * Tf;
-  c.ctas = (ny / 2) / ipc;
-  c.smem = ipc * bytes_per_inst;
-  return c;
-}
-
-// Persistent row kernels walk row pairs with a grid stride: at most
-// ctas_per_sm CTAs per SM (their register-limited residency).
-RowCfg persistent(RowCfg c, int ctas_per_sm) {
-  int sms = 0, dev = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (sms <= 0) sms = 1;
-  if (c.ctas > sms * ctas_per_sm) c.ctas = sms * ctas_per_sm;
-  return c;
-}
-
-// Column kernels of the step: ny/16 threads per column, NC columns per CTA,
-// NC a multiple of the layout's chunk width.
-ColCfg col_cfg(int nx, int ny, int chunk, size_t bytes_per_col, int max_threads) {
-  ColCfg c{};
-  const int Tc = ny / 16;
-  int C = 256 / Tc;
-  if (C < chunk) C = chunk;
-  if (C > nx / 2) C = nx / 2;
-  while (C > chunk && ((size_t)C * bytes_per_col > kSmemLimit || C * Tc > max_threads)) C /= 2;
-  c.cols_per_cta = C;
-  c.log2cols = ilog2(C);
-  c.threads = C * Tc;
-  c.ctas = (nx / 2) / C;
-  c.smem = (size_t)C * bytes_per_col;
-  return c;
-}
-
 // Diagnostic (structure factor) kernels: nx/8 or ny/8 threads per FFT.
 RowCfg sf_row_cfg(int nx, int ny, size_t bytes_per_inst) {
   RowCfg c{};
@@ -198,21 +156,62 @@ ColCfg sf_col_cfg(int nx, int ny, size_t bytes_per_row_per_col, size_t elem) {
   return c;
 }
 
-void configure_class(SizeClass& cl, int precision) {
-  const size_t R = precision == SHF_FP64 ? 8 : 4;   // real
-  const size_t Cx = 2 * R;                            // complex
-  const int chunk = precision == SHF_FP64 ? 1 : 2;    // x-spectral tile width (16 bytes)
-  const int nx = cl.nx, ny = cl.ny;
-  const size_t prow = (size_t)padded_len(nx) * Cx, pcol = (size_t)padded_len(ny) * Cx;
-  cl.stage1 = row_cfg(nx, ny, stage1_inst_bytes(nx, R));
-  cl.rowinv0 = persistent(row_cfg(nx, ny, prow), 2);
-  cl.rowinv1 = row_cfg(nx, ny, prow);
-  cl.stage2 = row_cfg(nx, ny, stage2_inst_bytes(nx, R));
-  const int colmax = precision == SHF_FP64 ? 256 : 512;   // the column kernels' launch bounds
-  cl.colphi = col_cfg(nx, ny, chunk, pcol, colmax);
-  cl.colflow = col_cfg(nx, ny, chunk, pcol, colmax);
+int sm_count() {
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+
+// Persistent transform kernels: nfft/8 threads per instance, instances per
+// CTA up to 512 threads; the grid holds as many CTAs as are resident at once
+// (occupancy query), shared over the members of the launch.
+template <class T>
+LaunchCfg persistent_cfg(int kind, int nfft, int max_inst, int items, size_t inst_bytes, int nmem) {
+  LaunchCfg c{};
+  const int Tf = nfft / kP;
+  int ipc = 512 / Tf;
+  if (ipc < 1) ipc = 1;
+  if (ipc > max_inst) ipc = max_inst;
+  while (ipc > 1 && ipc * inst_bytes > kSmemLimit) ipc /= 2;
+  c.inst_per_cta = ipc;
+  c.threads = ipc * Tf;
+  c.smem = ipc * inst_bytes;
+  const int work = (items + ipc - 1) / ipc;
+  const int resident = step_kernel_occupancy<T>(kind, c.threads, c.smem) * sm_count();
+  int g = (resident + nmem - 1) / nmem;
+  if (g > work) g = work;
+  c.grid_x = g < 1 ? 1 : g;
+  c.grid_y = 1;
+  return c;
+}
+
+template <class T>
+void configure_class_t(SizeClass& cl) {
+  const size_t R = sizeof(T), Cx = 2 * R;
+  const int nx = cl.nx, ny = cl.ny, nmem = (int)cl.members.size();
+  LaunchCfg st{};
+  st.grid_x = nx / (nx < 128 ? nx : 128);
+  st.grid_y = ny / 8;
+  st.threads = 256;
+  cl.cfg[KIND_STENCIL1] = st;
+  cl.cfg[KIND_STENCIL2] = st;
+  cl.cfg[KIND_ROWFWD_PHI] =
+      persistent_cfg<T>(KIND_ROWFWD_PHI, nx, ny / 2, 3 * (ny / 2), rowfwd_inst_bytes(nx, R), nmem);
+  cl.cfg[KIND_ROWFWD_G] = persistent_cfg<T>(KIND_ROWFWD_G, nx, ny / 2, ny / 2, rowfwd_inst_bytes(nx, R), nmem);
+  cl.cfg[KIND_COLPASS_PHI] =
+      persistent_cfg<T>(KIND_COLPASS_PHI, ny, nx / 2, nx / 2, colpass_inst_bytes(ny, R), nmem);
+  cl.cfg[KIND_COLPASS_FLOW] =
+      persistent_cfg<T>(KIND_COLPASS_FLOW, ny, nx / 2, nx / 2, colpass_inst_bytes(ny, R), nmem);
+  cl.cfg[KIND_ROWINV_PHI] = persistent_cfg<T>(KIND_ROWINV_PHI, nx, ny / 2, ny / 2, rowinv_inst_bytes(nx, R), nmem);
+  cl.cfg[KIND_ROWINV_FLOW] = persistent_cfg<T>(KIND_ROWINV_FLOW, nx, ny / 2, ny, rowinv_inst_bytes(nx, R), nmem);
   cl.sfrows = sf_row_cfg(nx, ny, nx * Cx);
   cl.sfcols = sf_col_cfg(nx, ny, Cx + 12, Cx);
+}
+
+void configure_class(SizeClass& cl, int precision) {
+  if (precision == SHF_FP64) configure_class_t<double>(cl);
+  else configure_class_t<float>(cl);
 }
 
 void host_strain(long long n, double gdot, double dt, int r, double* s, long long* K) {
@@ -237,6 +236,7 @@ MemberDesc make_desc(const shf_grid* o, const Member& m) {
   d.omega_star = m.omega_star;
   d.nyq_phi = m.nyq;
   d.nyq_omega = static_cast<char*>(m.nyq) + (size_t)m.ny * (o->precision == SHF_FP64 ? 8 : 4);
+  d.gbuf = m.phi_star;   // g is formed after phi^{n+1}, when phi* is no longer needed
   d.n = m.d_n;
   d.a = m.a; d.b = m.b; d.kappa = m.kappa; d.M = m.M; d.eta = m.eta; d.rho = m.rho;
   d.gdot = m.gdot; d.dt = m.dt; d.dx = m.dx;
@@ -397,7 +397,6 @@ int build(shf_grid* g, const std::vector<int>& nx, const std::vector<int>& ny, c
       cl.ny = m.ny;
       cl.log2nx = m.log2nx;
       cl.log2ny = m.log2ny;
-      configure_class(cl, g->precision);
       g->classes.push_back(cl);
       found = (int)g->classes.size() - 1;
     }
@@ -406,6 +405,7 @@ int build(shf_grid* g, const std::vector<int>& nx, const std::vector<int>& ny, c
     g->classes[found].members.push_back(r);
   }
   for (auto& cl : g->classes) {
+    configure_class(cl, g->precision);
     cl.h_desc.resize(cl.members.size());
     if (cudaMalloc(&cl.d_desc, cl.members.size() * sizeof(MemberDesc)) != cudaSuccess)
       return fail(g, SHF_ENOMEM, "descriptor allocation failed");
@@ -420,8 +420,8 @@ int build(shf_grid* g, const std::vector<int>& nx, const std::vector<int>& ny, c
   std::vector<double> tw(2 * NMAX);
   for (int k = 0; k < NMAX; ++k) unit_root(k, NMAX, &tw[2 * k], &tw[2 * k + 1]);
   std::vector<double> twr(2 * (size_t)stage_table_len());
-  for (int a : {4, 8})
-    for (int lr = 1; lr <= 4; ++lr) {
+  for (int a = 1; a <= 11; ++a)
+    for (int lr = 1; lr <= 4 && a + lr <= LOG2_NMAX; ++lr) {
       const long Ns = 1L << a, R = 1L << lr, L = Ns * R;
       for (long k = 0; k < Ns; ++k)
         for (long r = 0; r < R; ++r) {
@@ -450,22 +450,14 @@ int build(shf_grid* g, const std::vector<int>& nx, const std::vector<int>& ny, c
   return SHF_OK;
 }
 
-// The six launches of one step for one size class, in order (kind 0..5).
+// The launches of one step for one size class, in order (kind 0..KIND_COUNT-1).
 template <class T>
 void launch_kind(shf_grid* o, SizeClass& cl, int kind) {
   const cplx<T>* tw = static_cast<const cplx<T>*>(o->d_twr);
-  const int nm = (int)cl.members.size();
-  switch (kind) {
-    case 0: launch_stage1<T>(cl.d_desc, nm, cl.log2nx, cl.log2ny, tw, cl.stage1, o->stream); break;
-    case 1: launch_colpass_phi<T>(cl.d_desc, nm, cl.log2nx, cl.log2ny, tw, cl.colphi, o->stream); break;
-    case 2: launch_rowinv<T>(cl.d_desc, nm, cl.log2nx, cl.log2ny, tw, cl.rowinv0, 0, o->stream); break;
-    case 3: launch_stage2<T>(cl.d_desc, nm, cl.log2nx, cl.log2ny, tw, cl.stage2, o->stream); break;
-    case 4: launch_colpass_flow<T>(cl.d_desc, nm, cl.log2nx, cl.log2ny, tw, cl.colflow, o->stream); break;
-    default: launch_rowinv<T>(cl.d_desc, nm, cl.log2nx, cl.log2ny, tw, cl.rowinv1, 1, o->stream); break;
-  }
+  launch_step_kernel<T>(kind, cl.d_desc, (int)cl.members.size(), cl.log2nx, cl.log2ny, tw, cl.cfg[kind], o->stream);
 }
 
-constexpr int kKinds = 6;
+constexpr int kKinds = KIND_COUNT;
 
 template <class T>
 void enqueue_step(shf_grid* o) {

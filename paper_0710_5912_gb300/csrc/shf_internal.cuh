@@ -25,6 +25,7 @@ struct MemberDesc {
   void* omega_star;  // omega* (real, already remapped at a wrap)
   void* nyq_phi;     // per row: the real Nyquist coefficient of phi*'s row DFT
   void* nyq_omega;   // per row: the same for omega*
+  void* gbuf;        // g = -F/rho (or -F/eta), real; shares phi*'s storage (phi* is dead by then)
   long long* n;   // device step counter
   // parameters and derived constants (double; cast to the working precision)
   double a, b, kappa, M, eta, rho, gdot, dt, dx;
@@ -54,17 +55,45 @@ __device__ __forceinline__ void strain_dev(long long n, double gdot, double dt, 
   K = (long long)Kd;
 }
 
-// Shared memory of one row-pair instance of the stage kernels (real_bytes =
-// sizeof(T)): stage 1 holds the padded FFT buffer plus two cp.async tiles of
-// 2 fields x 4 rows x (nx/16 + 4); stage 2 the buffer plus two phi tiles of
-// 6 rows x (nx/16 + 6) and a mu tile of 4 rows x (nx/16 + 4).
-__host__ __device__ constexpr size_t stage1_inst_bytes(int nx, size_t real_bytes) {
-  return (size_t)padded_len(nx) * 2 * real_bytes + 2 * 2 * 4 * (size_t)(nx / 16 + 4) * real_bytes;
+// Shared memory of one instance of the persistent transform kernels (rounded
+// to 128 bytes so that every instance's staging buffer is 16-byte aligned):
+// rowfwd stages two real rows and holds the padded FFT buffer; colpass stages
+// two complex columns plus the buffer; rowinv stages the 32-byte chunks of a
+// row pair (nx complex) plus the buffer.
+__host__ __device__ constexpr size_t round128(size_t b) { return (b + 127) & ~(size_t)127; }
+__host__ __device__ constexpr size_t rowfwd_inst_bytes(int nx, size_t real_bytes) {
+  return round128(2 * (size_t)nx * real_bytes + (size_t)padded_len(nx) * 2 * real_bytes);
 }
-__host__ __device__ constexpr size_t stage2_inst_bytes(int nx, size_t real_bytes) {
-  return (size_t)padded_len(nx) * 2 * real_bytes +
-         (2 * 6 * (size_t)(nx / 16 + 6) + 4 * (size_t)(nx / 16 + 4)) * real_bytes;
+__host__ __device__ constexpr size_t colpass_inst_bytes(int ny, size_t real_bytes) {
+  return round128((2 * (size_t)ny + (size_t)padded_len(ny)) * 2 * real_bytes);
 }
+__host__ __device__ constexpr size_t rowinv_inst_bytes(int nx, size_t real_bytes) {
+  return round128(((size_t)nx + (size_t)padded_len(nx)) * 2 * real_bytes);
+}
+
+// The eight launches of a step, in order.
+enum StepKind {
+  KIND_STENCIL1 = 0,
+  KIND_ROWFWD_PHI = 1,
+  KIND_COLPASS_PHI = 2,
+  KIND_ROWINV_PHI = 3,
+  KIND_STENCIL2 = 4,
+  KIND_ROWFWD_G = 5,
+  KIND_COLPASS_FLOW = 6,
+  KIND_ROWINV_FLOW = 7,
+  KIND_COUNT = 8
+};
+
+struct LaunchCfg {
+  int grid_x, grid_y;   // grid (the member index is the last grid dimension)
+  int threads;
+  size_t smem;          // dynamic shared memory bytes
+  int inst_per_cta;     // transform instances per CTA (persistent kinds)
+};
+
+template <class T> void launch_step_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int log2ny,
+                                           const cplx<T>* tw, const LaunchCfg& c, cudaStream_t st);
+template <class T> int step_kernel_occupancy(int kind, int threads, size_t smem);
 
 // ---- kernel launchers (step_kernels.cu / diag_kernels.cu) ----
 struct RowCfg {
@@ -80,19 +109,6 @@ struct ColCfg {
   int ctas;
   size_t smem;
 };
-
-template <class T> void launch_stage1(const MemberDesc* d, int nmem, int log2nx, int log2ny,
-                                      const cplx<T>* tw, const RowCfg& c, cudaStream_t st);
-template <class T> void launch_colpass_phi(const MemberDesc* d, int nmem, int log2nx, int log2ny,
-                                           const cplx<T>* tw, const ColCfg& c, cudaStream_t st);
-// mode 0: phi rows pairs (x-spectral phi -> real phi, remap shift); mode 1:
-// final flow (psi,omega same row for inertial members, psi row pairs for Stokes)
-template <class T> void launch_rowinv(const MemberDesc* d, int nmem, int log2nx, int log2ny,
-                                      const cplx<T>* tw, const RowCfg& c, int mode, cudaStream_t st);
-template <class T> void launch_stage2(const MemberDesc* d, int nmem, int log2nx, int log2ny,
-                                      const cplx<T>* tw, const RowCfg& c, cudaStream_t st);
-template <class T> void launch_colpass_flow(const MemberDesc* d, int nmem, int log2nx, int log2ny,
-                                            const cplx<T>* tw, const ColCfg& c, cudaStream_t st);
 
 template <class T> void launch_convert_in(const double* src, T* dst, long long count, cudaStream_t st);
 template <class T> void launch_convert_out(const T* src, double* dst, long long count, cudaStream_t st);

@@ -1,63 +1,58 @@
 // Kernels of one time step (Appendix B of arXiv:0710.5912), templated on the
-// working precision T (float or double).  A step is six launches:
+// working precision T (float or double).  A step is eight launches per grid
+// size:
 //
-//   stage1       item 1 + item 2's advection at s = s^n: phi* = phi - dt J(psi, phi),
-//                omega* = omega - dt J(psi, omega) (Eq. advective with the Eq. p1y
-//                stencils), f = phi^3; phi*, omega* are kept in real space and
-//                their row (x) transforms, with f's, go to x-spectral buffers.
-//   colpass_phi  column (y) transforms of phi*, f and the Cahn-Hilliard update
-//                of item 1 in the paper's increment form
+//   stencil1     item 1 + item 2's advection at s = s^n (Eq. advective with the
+//                Eq. p1y stencils): phi* = phi - dt J(psi, phi) and omega* =
+//                omega - dt J(psi, omega), real; omega* is written at the
+//                relabelled positions when the strain wraps during the step.
+//   rowfwd_phi   row (x) transforms of (phi*, f = phi^3) per row and of the
+//                omega* row pair -> x-spectral buffers, plus each row's real
+//                Nyquist coefficient of phi* and omega*.
+//   colpass_phi  column (y) transforms of phi*, f; the Cahn-Hilliard update of
+//                item 1 in the paper's increment form
 //                  phi^{n+1} = phi* + (1 + D4/2)^-1 (-D2 phi* - D4 phi* + D2 f),
-//                Nyquist modes of phi^{n+1} zeroed; the increment is transformed
-//                back along y.
-//   rowinv_phi   inverse row transform of the increment, phi^{n+1} = phi* + inc
-//                (minus phi*'s Nyquist column); at a strain wrap the row-shift
-//                remap is applied as a permutation of the writes.
-//   stage2       mu = -a phi + b phi^3 - kappa lap_c phi and the body-force curl
-//                F = d_x phi d_y mu - d_y phi d_x mu at s = s^{n+1} (Eq. G), g =
-//                -F/rho (or -F/eta for Stokes), row transform.
+//                Nyquist modes of phi^{n+1} zeroed; the increment back along y.
+//   rowinv_phi   phi^{n+1} = phi* + row inverse of the increment (minus phi*'s
+//                Nyquist column), written at the relabelled positions at a wrap.
+//   stencil2     mu = -a phi + b phi^3 - kappa lap_c phi and the body-force curl
+//                F = d_x phi d_y mu - d_y phi d_x mu at s = s^{n+1} (Eq. G);
+//                g = -F/rho, or -F/eta for Stokes, real.
+//   rowfwd_g     row transforms of g row pairs.
 //   colpass_flow column transforms; Crank-Nicolson vorticity update in increment
 //                form omega^{n+1} = omega* + (1 - C/2)^-1 (C omega* + g) and the
 //                Poisson solve psi = omega / k^2 (items 2-3), or the Stokes solve
 //                psi = g / k^4; inverse column transforms.
-//   rowinv_flow  inverse row transforms: psi, and omega^{n+1} = omega* + inc;
-//                advances the step counter.
+//   rowinv_flow  psi rows, and omega^{n+1} = omega* + row inverse of the
+//                increment; advances the step counter.
 //
-// Transforming only the increments keeps the FP32 rounding of every step
+// Transforming only the increments keeps the FP32 rounding of a step
 // proportional to the change of the field instead of to the field itself.
+//
+// Execution: the stencils run on 2D tiles; the transform kernels are
+// persistent -- every instance walks its work items (row pairs or columns) with
+// a grid stride and, while transforming one item, streams the next item's
+// input into a shared-memory staging buffer with cp.async, so the loads in
+// flight hold shared memory rather than registers.  The FFT itself keeps 8
+// points per thread in registers (fft_block.cuh).
 //
 // Layout: real fields ny x nx row-major.  x-spectral buffers hold, for each row
 // j, the modes m = 0..nx/2-1 of the row's real DFT (the Nyquist column is
 // carried separately as one real per row), tiled in chunks of CL = 2^LC
 // adjacent modes: element (j, m) sits at ((m >> LC) ny + j) CL + (m & (CL-1)),
-// so a column pass reads whole chunks contiguously and a pair of rows writes
-// 2 CL adjacent values.  The 1/(nx ny) of the inverse transforms is applied in
-// the column passes.  Each launch covers a batch of members (blockIdx.y).
+// so a chunk of a row pair is 32 contiguous bytes and a column is one strided
+// run.  The 1/(nx ny) of the inverse transforms is applied in the column passes.
+// Each launch covers a batch of members of one size (one descriptor each).
 #include "shf_internal.cuh"
 
 namespace shf {
 
-template <class T>
-__device__ __forceinline__ T ldf(const T* __restrict__ f, int i, int j, int mx, int my, int l2x) {
-  return __ldg(f + (((j & my) << l2x) | (i & mx)));
-}
+// minimum resident CTAs per SM requested from the compiler (caps registers)
+template <class T> constexpr int min_ctas() { return sizeof(T) == 8 ? 1 : 2; }
 
-// Sheared y-derivative of Eq. p1y: the vertical central difference blended
-// (weight |s|/2) with the difference across the diagonal pair two cells away;
-// d = -2 for s >= 0 (pair (i-2, j+1), (i+2, j-1)), d = +2 for s < 0.
-template <class T>
-__device__ __forceinline__ T dy_sheared(const T* __restrict__ f, int i, int j, int mx, int my, int l2x,
-                                        T w0, T w1, int d, T inv2h) {
-  const T vert = ldf(f, i, j + 1, mx, my, l2x) - ldf(f, i, j - 1, mx, my, l2x);
-  const T diag = ldf(f, i + d, j + 1, mx, my, l2x) - ldf(f, i - d, j - 1, mx, my, l2x);
-  return (w0 * vert + w1 * diag) * inv2h;
-}
-
-template <class T>
-__device__ __forceinline__ T dx_central(const T* __restrict__ f, int i, int j, int mx, int my, int l2x,
-                                        T inv2h) {
-  return (ldf(f, i + 1, j, mx, my, l2x) - ldf(f, i - 1, j, mx, my, l2x)) * inv2h;
-}
+template <class T> struct Layout;
+template <> struct Layout<float> { static constexpr int LC = 1; };   // 2 complex floats = 16 B
+template <> struct Layout<double> { static constexpr int LC = 0; };  // 1 complex double = 16 B
 
 // cells by which row j moves at a wrap: ((K1 - K0) r j) mod nx
 __device__ __forceinline__ int remap_shift(long long dK, int r, int j, int nx) {
@@ -71,6 +66,46 @@ __device__ __forceinline__ size_t xs_idx(int j, int m, int ny, int LC) {
   return ((((size_t)(m >> LC) * ny) + j) << LC) | (size_t)(m & ((1 << LC) - 1));
 }
 
+// Strain s, wrap flag and the weights of the sheared y-derivative (Eq. p1y):
+// D_y^s f = [w0 (f(i, j+1) - f(i, j-1)) + w1 (f(i+d, j+1) - f(i-d, j-1))] / 2h,
+// w1 = |s|/2, w0 = 1 - w1, d = -2 for s >= 0 and +2 for s < 0.
+template <class T>
+struct Shear {
+  T s, w0, w1;
+  int d;
+  long long dK;   // K(n+1) - K(n): nonzero when the strain wraps during the step
+  __device__ __forceinline__ Shear(const MemberDesc& D, long long n) {
+    double sd, s1;
+    long long K0, K1;
+    strain_dev(n, D.gdot, D.dt, D.ratio, sd, K0);
+    strain_dev(n + 1, D.gdot, D.dt, D.ratio, s1, K1);
+    s = (T)sd;
+    w1 = (s < T(0) ? -s : s) * T(0.5);
+    w0 = T(1) - w1;
+    d = s >= T(0) ? -2 : 2;
+    dK = K1 - K0;
+  }
+};
+
+// ---- asynchronous global -> shared copies (cp.async; the wait is a hardware
+// instruction, not a spin loop)
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async16(void* s, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* s, const void* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// bytes (a multiple of 16, both ends 16-byte aligned) from src to dst
+__device__ __forceinline__ void copy_async(void* dst, const void* src, int bytes, int t, int nthr) {
+  char* d = static_cast<char*>(dst);
+  const char* s = static_cast<const char*>(src);
+  for (int off = t * 16; off < bytes; off += nthr * 16) cp_async16(d + off, s + off);
+}
+
 // Half spectra of two real rows a, b from Z = FFT(a + i b) held in a padded
 // buffer: A[m] = (Z[m] + conj Z[N-m]) / 2, B[m] = (Z[m] - conj Z[N-m]) / (2i).
 template <class C>
@@ -82,97 +117,26 @@ __device__ __forceinline__ void split_pair(const C* z, int m, int mx, C& A, C& B
   B = C{(zk.y - zc.y) * T(0.5), -(zk.x - zc.x) * T(0.5)};
 }
 
-// Writes the half spectra of rows (j0, j0+1) split from Z = FFT(a + i b):
-//   pair_of_rows = true : z0 holds (row j0, row j0+1) of one field -> dst
-//   pair_of_rows = false: z0 holds (field1, field2) of row j0 and z1 of row j0+1
-//                         -> field1 to dst, field2 to dst2
-// Each thread writes whole chunks: 2 CL adjacent elements (rows j0 and j0+1).
+// Z holds FFT(row j0 + i row j0+1) of one field: both half spectra -> dst,
+// whole 2 CL-element chunks per thread.
 template <int LC, class C>
-__device__ __forceinline__ void write_pair_rows(const C* z0, const C* z1, bool pair_of_rows, C* dst, C* dst2,
-                                                int j0, int nx, int ny, int t, int Tthreads) {
+__device__ __forceinline__ void write_pair_rows(const C* z, C* dst, int j0, int nx, int ny, int t, int Tthreads) {
   constexpr int CL = 1 << LC;
   const int mx = nx - 1;
   const int nchunk = (nx >> 1) >> LC;
   for (int cb = t; cb < nchunk; cb += Tthreads) {
-    C r0[CL], r1[CL], s0[CL], s1[CL];
-#pragma unroll
-    for (int c = 0; c < CL; ++c) {
-      const int m = (cb << LC) + c;
-      if (pair_of_rows) {
-        split_pair(z0, m, mx, r0[c], r1[c]);
-      } else {
-        split_pair(z0, m, mx, r0[c], s0[c]);
-        split_pair(z1, m, mx, r1[c], s1[c]);
-      }
-    }
     C* p = dst + ((((size_t)cb * ny) + j0) << LC);
 #pragma unroll
     for (int c = 0; c < CL; ++c) {
-      p[c] = r0[c];
-      p[CL + c] = r1[c];
-    }
-    if (!pair_of_rows) {
-      C* p2 = dst2 + ((((size_t)cb * ny) + j0) << LC);
-#pragma unroll
-      for (int c = 0; c < CL; ++c) {
-        p2[c] = s0[c];
-        p2[CL + c] = s1[c];
-      }
+      C A, B;
+      split_pair(z, (cb << LC) + c, mx, A, B);
+      p[c] = A;
+      p[CL + c] = B;
     }
   }
 }
 
-// Launch bounds: row kernels run 256 threads; the minimum CTAs per SM caps
-// registers so that several CTAs (as many as shared memory allows) co-reside.
-// Column kernels run up to 512 threads in float and 256 in double.
-template <class T> constexpr int col_threads() { return sizeof(T) == 8 ? 256 : 512; }
-template <class T> constexpr int min_ctas(int fp32, int fp64) { return sizeof(T) == 8 ? fp64 : fp32; }
-
-template <class T> struct Layout;
-template <> struct Layout<float> { static constexpr int LC = 1; };   // 2 complex floats = 16 B
-template <> struct Layout<double> { static constexpr int LC = 0; };  // 1 complex double = 16 B
-
-// ---- asynchronous global -> shared copies of single elements (cp.async)
-template <class T>
-__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  if (sizeof(T) == 4) asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-  else asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-// Tile of NF fields x R rows (r0 .. r0+R-1) x W columns (x0 .. x0+W-1), all
-// indices periodic, element (f, r, x) at tile[(f R + r) W + x]; issued by the
-// nthreads threads of one instance.
-template <class T, int NF>
-__device__ __forceinline__ void load_tile_async(T* tile, const T* const (&fld)[NF], int r0, int R, int x0, int W,
-                                                int mx, int my, int l2x, int t, int nthreads) {
-#pragma unroll
-  for (int fi = 0; fi < NF; ++fi)
-    for (int r = 0; r < R; ++r) {
-      const T* row = fld[fi] + ((size_t)((r0 + r) & my) << l2x);
-      T* dst = tile + (fi * R + r) * W;
-      for (int x = t; x < W; x += nthreads) cp_async_elem(dst + x, row + ((x0 + x) & mx));
-    }
-}
-
-// Sheared y-derivative (Eq. p1y) and central x-derivative on a tile row r,
-// local column x (tile row pitch W).
-template <class T>
-__device__ __forceinline__ T tile_dy(const T* tl, int r, int x, int W, T w0, T w1, int d, T inv2h) {
-  const T vert = tl[(r + 1) * W + x] - tl[(r - 1) * W + x];
-  const T diag = tl[(r + 1) * W + x + d] - tl[(r - 1) * W + x - d];
-  return (w0 * vert + w1 * diag) * inv2h;
-}
-template <class T>
-__device__ __forceinline__ T tile_dx(const T* tl, int r, int x, int W, T inv2h) {
-  return (tl[r * W + x + 1] - tl[r * W + x - 1]) * inv2h;
-}
-
-// Half spectra of one row from Z = FFT(a + i b) (a, b the row of two fields):
-// field a -> dstA, field b -> dstB, whole chunks of CL modes per thread.
+// Z holds FFT(a + i b) of row j of two fields: a -> dstA, b -> dstB.
 template <int LC, class C>
 __device__ __forceinline__ void write_one_row(const C* z, C* dstA, C* dstB, int j, int nx, int ny, int t,
                                               int Tthreads) {
@@ -194,336 +158,411 @@ __device__ __forceinline__ void write_one_row(const C* z, C* dstA, C* dstB, int 
 
 // v[q] = Z[t + T q] from a padded buffer (the register layout of fft_reg)
 template <class C>
-__device__ __forceinline__ void smem_to_reg(C (&v)[16], const C* Z, int log2N, int t) {
-  const int T = 1 << (log2N - 4);
+__device__ __forceinline__ void smem_to_reg(C (&v)[kP], const C* Z, int log2N, int t) {
+  const int T = 1 << (log2N - kLogP);
 #pragma unroll
-  for (int q = 0; q < 16; ++q) v[q] = Z[pad16(t + q * T)];
+  for (int q = 0; q < kP; ++q) v[q] = Z[pad16(t + q * T)];
 }
 
-// ----------------------------------------------------------------- stage 1
-// One instance = a pair of rows (j0, j1), Tf = nx/16 threads; register q of
-// thread t is point i = Tf q + t, so each q is a chunk of Tf consecutive
-// points whose stencil inputs (4 rows, Tf + 4 columns) are staged in shared
-// memory by cp.async, one chunk ahead.  Three passes: row j0 (phi*, f), row j1
-// (phi*, f), rows j0 and j1 of omega* (inertial members only).
-template <class T>
-__global__ void __launch_bounds__(256, min_ctas<T>(2, 1)) k_stage1(const MemberDesc* __restrict__ descs, int log2nx,
-                                                                    int log2ny, const cplx<T>* __restrict__ tw) {
-  using C = cplx<T>;
-  constexpr int LC = Layout<T>::LC;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const MemberDesc& D = descs[blockIdx.y];
-  const int nx = 1 << log2nx, ny = 1 << log2ny, mx = nx - 1, my = ny - 1;
-  const int Tf = nx >> 4;
-  const int inst = threadIdx.x / Tf, t = threadIdx.x - inst * Tf;
-  const int j0 = 2 * (blockIdx.x * (blockDim.x / Tf) + inst), j1 = j0 + 1;
-  const int W = Tf + 4;
-  unsigned char* base = smem_raw + (size_t)inst * stage1_inst_bytes(nx, sizeof(T));
-  C* Z = reinterpret_cast<C*>(base);
-  T* tiles = reinterpret_cast<T*>(base + (size_t)padded_len(nx) * sizeof(C));
-  const int tsz = 2 * 4 * W;
+// Number of loop iterations of a persistent CTA: every instance of the CTA runs
+// the same count (the loop body has barriers); an instance whose item is past
+// the end idles through its last iteration.
+__device__ __forceinline__ int persistent_iters(int nitems, int ipc) {
+  const int stride = gridDim.x * ipc;
+  const int first = blockIdx.x * ipc;
+  return first < nitems ? (nitems - first + stride - 1) / stride : 0;
+}
 
-  const long long n = *D.n;
-  double s_d, s1_d;
-  long long K0, K1;
-  strain_dev(n, D.gdot, D.dt, D.ratio, s_d, K0);
-  strain_dev(n + 1, D.gdot, D.dt, D.ratio, s1_d, K1);
-  const T s = (T)s_d;
-  const T w1 = (s < T(0) ? -s : s) * T(0.5);
-  const T w0 = T(1) - w1;
-  const int d = s >= T(0) ? -2 : 2;
-  const T dt = (T)D.dt, inv2h = (T)D.inv_2h;
+// ============================================================== stencils
+// 2D tiles of TX x TY outputs (TX = min(nx, 128), a template constant so that
+// every tile index is divided by a constant; TY = 8), 256 threads.
+constexpr int kTY = 8;
+
+// stage-1 stencil: inputs phi, psi (and omega) with halo x +-2, y +-1
+template <class T, int TX>
+__global__ void __launch_bounds__(256) k_stencil1(const MemberDesc* __restrict__ descs, int log2nx, int log2ny) {
+  constexpr int W = TX + 4;
+  __shared__ T sh[3][kTY + 2][W];
+  const MemberDesc& D = descs[blockIdx.z];
+  const int nx = 1 << log2nx, ny = 1 << log2ny, mx = nx - 1, my = ny - 1;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * kTY;
   const bool stokes = D.stokes != 0;
-  const bool wrap = D.remap && (K1 != K0);
-  const T* __restrict__ phi = static_cast<const T*>(D.phi);
-  const T* __restrict__ psi = static_cast<const T*>(D.psi);
-  const T* __restrict__ om = static_cast<const T*>(D.omega);
+  const Shear<T> sc(D, *D.n);
+  const T dt = (T)D.dt, inv2h = (T)D.inv_2h;
+  const T* __restrict__ f0 = static_cast<const T*>(D.phi);
+  const T* __restrict__ f1 = static_cast<const T*>(D.psi);
+  const T* __restrict__ f2 = static_cast<const T*>(D.omega);
+  for (int e = threadIdx.x; e < (kTY + 2) * W; e += blockDim.x) {
+    const int r = e / W, c = e - r * W;
+    const size_t g = ((size_t)((y0 - 1 + r) & my) << log2nx) + ((x0 - 2 + c) & mx);
+    sh[0][r][c] = __ldg(f0 + g);
+    sh[1][r][c] = __ldg(f1 + g);
+    if (!stokes) sh[2][r][c] = __ldg(f2 + g);
+  }
+  __syncthreads();
   T* phis = static_cast<T*>(D.phi_star);
   T* oms = static_cast<T*>(D.omega_star);
-  const int npass = stokes ? 2 : 3;
-
-  C v[16];
-#pragma unroll 1
-  for (int pass = 0; pass < npass; ++pass) {
-    const bool wpass = pass == 2;
-    if (wpass && wrap) {
-      // omega* at a wrap: evaluated at the source of every remapped position,
-      // gathered through Z (a rolled loop: this path runs once per wrap)
-      const int sh0 = remap_shift(K1 - K0, D.ratio, j0, nx);
-      const int sh1 = remap_shift(K1 - K0, D.ratio, j1, nx);
-#pragma unroll 1
-      for (int p = t; p < nx; p += Tf) {
-        T ws[2];
-#pragma unroll
-        for (int jj = 0; jj < 2; ++jj) {
-          const int j = j0 + jj;
-          const int i = (p - (jj ? sh1 : sh0)) & mx;
-          const T dxpsi = dx_central(psi, i, j, mx, my, log2nx, inv2h);
-          const T dypsi = dy_sheared(psi, i, j, mx, my, log2nx, w0, w1, d, inv2h);
-          const T dxw = dx_central(om, i, j, mx, my, log2nx, inv2h);
-          const T dyw = dy_sheared(om, i, j, mx, my, log2nx, w0, w1, d, inv2h);
-          ws[jj] = ldf(om, i, j, mx, my, log2nx) - dt * (dypsi * dxw - dxpsi * dyw);
-          oms[((size_t)j << log2nx) + p] = ws[jj];
-        }
-        Z[pad16(p)] = C{ws[0], ws[1]};
-      }
-      __syncthreads();
-      smem_to_reg(v, Z, log2nx, t);
-      __syncthreads();
-    } else {
-      const T* fld[2] = {wpass ? psi : phi, wpass ? om : psi};
-      load_tile_async<T, 2>(tiles, fld, j0 - 1, 4, -2, W, mx, my, log2nx, t, Tf);
-      cp_async_commit();
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        if (q + 1 < 16) {
-          load_tile_async<T, 2>(tiles + ((q + 1) & 1) * tsz, fld, j0 - 1, 4, Tf * (q + 1) - 2, W, mx, my, log2nx,
-                                t, Tf);
-          cp_async_commit();
-          cp_async_wait<1>();
-        } else {
-          cp_async_wait<0>();
-        }
-        __syncthreads();
-        const T* ta = tiles + (q & 1) * tsz;        // field 0: phi (or psi)
-        const T* tb = ta + 4 * W;                   // field 1: psi (or omega)
-        const int x = t + 2;
-        const int i = Tf * q + t;
-        if (!wpass) {
-          const int r = pass + 1;                   // tile row of j0 or j1
-          const T pc = ta[r * W + x];
-          const T dxphi = tile_dx(ta, r, x, W, inv2h);
-          const T dyphi = tile_dy(ta, r, x, W, w0, w1, d, inv2h);
-          const T dxpsi = tile_dx(tb, r, x, W, inv2h);
-          const T dypsi = tile_dy(tb, r, x, W, w0, w1, d, inv2h);
-          const T phistar = pc - dt * (dypsi * dxphi - dxpsi * dyphi);
-          phis[((size_t)(j0 + pass) << log2nx) + i] = phistar;
-          v[q] = C{phistar, (pc * pc) * pc};
-        } else {
-          T ws[2];
-#pragma unroll
-          for (int jj = 0; jj < 2; ++jj) {
-            const int r = jj + 1;
-            const T dxpsi = tile_dx(ta, r, x, W, inv2h);
-            const T dypsi = tile_dy(ta, r, x, W, w0, w1, d, inv2h);
-            const T dxw = tile_dx(tb, r, x, W, inv2h);
-            const T dyw = tile_dy(tb, r, x, W, w0, w1, d, inv2h);
-            ws[jj] = tb[r * W + x] - dt * (dypsi * dxw - dxpsi * dyw);
-            oms[((size_t)(j0 + jj) << log2nx) + i] = ws[jj];
-          }
-          v[q] = C{ws[0], ws[1]};
-        }
-        __syncthreads();                            // tile (q & 1) may now be refilled
-      }
+  const bool wrap = D.remap && sc.dK != 0;
+  for (int e = threadIdx.x; e < kTY * TX; e += blockDim.x) {
+    const int ly = e / TX, lx = e - ly * TX;
+    const int r = ly + 1, c = lx + 2;
+    const int y = y0 + ly, x = x0 + lx;
+    auto dxf = [&](int f) { return (sh[f][r][c + 1] - sh[f][r][c - 1]) * inv2h; };
+    auto dyf = [&](int f) {
+      return (sc.w0 * (sh[f][r + 1][c] - sh[f][r - 1][c]) +
+              sc.w1 * (sh[f][r + 1][c + sc.d] - sh[f][r - 1][c - sc.d])) * inv2h;
+    };
+    const T dxpsi = dxf(1), dypsi = dyf(1);
+    const T pc = sh[0][r][c];
+    phis[((size_t)y << log2nx) + x] = pc - dt * (dypsi * dxf(0) - dxpsi * dyf(0));
+    if (!stokes) {
+      const T ws = sh[2][r][c] - dt * (dypsi * dxf(2) - dxpsi * dyf(2));
+      const int sh_y = wrap ? remap_shift(sc.dK, D.ratio, y, nx) : 0;
+      oms[((size_t)y << log2nx) + ((x + sh_y) & mx)] = ws;
     }
-    fft_reg<false>(v, log2nx, t, Z, tw);
-    reg_to_smem(v, log2nx, t, Z);
-    if (!wpass) {
-      write_one_row<LC>(Z, static_cast<C*>(D.xs_phi), static_cast<C*>(D.xs_f), j0 + pass, nx, ny, t, Tf);
-      if (t == 0) static_cast<T*>(D.nyq_phi)[j0 + pass] = Z[pad16(nx >> 1)].x;   // phi*'s row Nyquist
-    } else {
-      write_pair_rows<LC>(Z, Z, true, static_cast<C*>(D.xs_w), static_cast<C*>(nullptr), j0, nx, ny, t, Tf);
-      if (t == 0) {
-        const C zn = Z[pad16(nx >> 1)];
-        static_cast<T*>(D.nyq_omega)[j0] = zn.x;
-        static_cast<T*>(D.nyq_omega)[j1] = zn.y;
-      }
-    }
-    __syncthreads();                                // Z is reused by the next pass
   }
 }
 
-// ------------------------------------------------------------ column passes
-// CTA: NC = 2^log2nc adjacent columns m0..m0+NC-1 (NC a multiple of the chunk
-// width); thread (c, t) with c = threadIdx.x mod NC handles column m0 + c,
-// points n = t + Tc q.  Loads and stores are contiguous across the warp.
+// stage-2 stencil: mu on a halo tile (x +-2, y +-1) from phi (x +-3, y +-2),
+// then g = c_force (d_x phi d_y mu - d_y phi d_x mu)
+template <class T, int TX>
+__global__ void __launch_bounds__(256) k_stencil2(const MemberDesc* __restrict__ descs, int log2nx, int log2ny) {
+  constexpr int WP = TX + 6, WM = TX + 4;
+  __shared__ T sp[kTY + 4][WP];
+  __shared__ T sm[kTY + 2][WM];
+  const MemberDesc& D = descs[blockIdx.z];
+  const int nx = 1 << log2nx, ny = 1 << log2ny, mx = nx - 1, my = ny - 1;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * kTY;
+  const Shear<T> sc(D, *D.n + 1);                        // s^{n+1}
+  const T a = (T)D.a, b = (T)D.b, kappa = (T)D.kappa;
+  const T inv2h = (T)D.inv_2h, ih2 = (T)D.inv_h2, i4h2 = (T)D.inv_4h2;
+  const T cxx = T(1) + sc.s * sc.s, cxy = T(2) * sc.s;
+  const T cf = (T)D.c_force;
+  const T* __restrict__ phi = static_cast<const T*>(D.phi);
+  for (int e = threadIdx.x; e < (kTY + 4) * WP; e += blockDim.x) {
+    const int r = e / WP, c = e - r * WP;
+    sp[r][c] = __ldg(phi + ((size_t)((y0 - 2 + r) & my) << log2nx) + ((x0 - 3 + c) & mx));
+  }
+  __syncthreads();
+  // mu (Appendix B item 2: 3-point second differences, 4-point cross difference)
+  for (int e = threadIdx.x; e < (kTY + 2) * WM; e += blockDim.x) {
+    const int r = e / WM, c = e - r * WM;
+    const int pr = r + 1, pcc = c + 1;
+    const T pc = sp[pr][pcc];
+    const T dxx = (sp[pr][pcc + 1] - T(2) * pc + sp[pr][pcc - 1]) * ih2;
+    const T dyy = (sp[pr + 1][pcc] - T(2) * pc + sp[pr - 1][pcc]) * ih2;
+    const T dxy = (sp[pr + 1][pcc + 1] - sp[pr - 1][pcc + 1] - sp[pr + 1][pcc - 1] + sp[pr - 1][pcc - 1]) * i4h2;
+    const T lap = cxx * dxx - cxy * dxy + dyy;
+    sm[r][c] = -a * pc + b * ((pc * pc) * pc) - kappa * lap;
+  }
+  __syncthreads();
+  T* g = static_cast<T*>(D.gbuf);
+  for (int e = threadIdx.x; e < kTY * TX; e += blockDim.x) {
+    const int ly = e / TX, lx = e - ly * TX;
+    const int rp = ly + 2, cp = lx + 3, rm = ly + 1, cm = lx + 2;
+    const T dxphi = (sp[rp][cp + 1] - sp[rp][cp - 1]) * inv2h;
+    const T dyphi = (sc.w0 * (sp[rp + 1][cp] - sp[rp - 1][cp]) +
+                     sc.w1 * (sp[rp + 1][cp + sc.d] - sp[rp - 1][cp - sc.d])) * inv2h;
+    const T dxmu = (sm[rm][cm + 1] - sm[rm][cm - 1]) * inv2h;
+    const T dymu = (sc.w0 * (sm[rm + 1][cm] - sm[rm - 1][cm]) +
+                    sc.w1 * (sm[rm + 1][cm + sc.d] - sm[rm - 1][cm - sc.d])) * inv2h;
+    g[((size_t)(y0 + ly) << log2nx) + x0 + lx] = cf * (dxphi * dymu - dyphi * dxmu);
+  }
+}
+
+// ====================================================== forward row transforms
+// Work items: mode 0 (phi): per row pair p, item 0 = (phi*, f) of row 2p,
+// item 1 = the same of row 2p+1, item 2 = omega* of rows (2p, 2p+1) for
+// inertial members; mode 1 (g): one item per row pair.  Each item stages two
+// real rows (a, b) in shared memory; the transform is of a + i b (for f the
+// cube of the staged phi row is taken on the fly).
 template <class T>
-__global__ void __launch_bounds__(col_threads<T>()) k_colpass_phi(const MemberDesc* __restrict__ descs, int log2nx,
-                                                      int log2ny, int log2nc, const cplx<T>* __restrict__ tw) {
+__global__ void __launch_bounds__(512, min_ctas<T>()) k_rowfwd(const MemberDesc* __restrict__ descs, int log2nx, int log2ny,
+                                                const cplx<T>* __restrict__ tw, int mode) {
   using C = cplx<T>;
   constexpr int LC = Layout<T>::LC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const MemberDesc& D = descs[blockIdx.y];
-  const int ny = 1 << log2ny;
-  const int Tc = ny >> 4;
-  const int c = threadIdx.x & ((1 << log2nc) - 1), t = threadIdx.x >> log2nc;
-  const int m = (blockIdx.x << log2nc) + c;
-  C* buf = reinterpret_cast<C*>(smem_raw) + (size_t)c * padded_len(ny);
-  C* xp = static_cast<C*>(D.xs_phi);
-  const C* xf = static_cast<const C*>(D.xs_f);
-  C vp[16], vf[16];
+  const int nx = 1 << log2nx, ny = 1 << log2ny;
+  const int Tf = nx >> kLogP;
+  const int ipc = blockDim.x / Tf;
+  const int inst = threadIdx.x / Tf, t = threadIdx.x - inst * Tf;
+  const int nsub = mode == 0 ? (D.stokes ? 2 : 3) : 1;
+  const int nitems = (ny >> 1) * nsub;
+  const int stride = gridDim.x * ipc;
+  unsigned char* base = smem_raw + (size_t)inst * rowfwd_inst_bytes(nx, sizeof(T));
+  T* stage = reinterpret_cast<T*>(base);
+  C* Z = reinterpret_cast<C*>(base + 2 * (size_t)nx * sizeof(T));
+  const T* phis = static_cast<const T*>(D.phi_star);
+  const T* phi = static_cast<const T*>(D.phi);
+  const T* oms = static_cast<const T*>(D.omega_star);
+  const T* gb = static_cast<const T*>(D.gbuf);
+
+  auto issue = [&](int w) {
+    if (w < nitems) {
+      const int p = w / nsub, sub = w - p * nsub;
+      const T *ra, *rb;
+      if (mode == 1) {
+        ra = gb + ((size_t)(2 * p) << log2nx);
+        rb = gb + ((size_t)(2 * p + 1) << log2nx);
+      } else if (sub < 2) {
+        ra = phis + ((size_t)(2 * p + sub) << log2nx);
+        rb = phi + ((size_t)(2 * p + sub) << log2nx);
+      } else {
+        ra = oms + ((size_t)(2 * p) << log2nx);
+        rb = oms + ((size_t)(2 * p + 1) << log2nx);
+      }
+      copy_async(stage, ra, nx * (int)sizeof(T), t, Tf);
+      copy_async(stage + nx, rb, nx * (int)sizeof(T), t, Tf);
+    }
+    cp_async_commit();
+  };
+
+  const int iters = persistent_iters(nitems, ipc);
+  int w = blockIdx.x * ipc + inst;
+  issue(w);
+  for (int it = 0; it < iters; ++it, w += stride) {
+    const bool active = w < nitems;
+    const int p = w / nsub, sub = w - p * nsub;
+    const bool cube = mode == 0 && sub < 2;
+    cp_async_wait_all();
+    __syncthreads();
+    C v[kP];
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const size_t g = xs_idx(t + q * Tc, m, ny, LC);
-    vp[q] = xp[g];
-    vf[q] = xf[g];
+    for (int q = 0; q < kP; ++q) {
+      const int i = t + q * Tf;
+      const T a = stage[i], bb = stage[nx + i];
+      v[q] = C{a, cube ? (bb * bb) * bb : bb};
+    }
+    __syncthreads();                                    // stage free
+    issue(w + stride);                                  // next item streams in during the transform
+    fft_reg<false>(v, log2nx, t, Z, tw);
+    reg_to_smem(v, log2nx, t, Z);
+    if (active) {
+      if (mode == 1) {
+        write_pair_rows<LC>(Z, static_cast<C*>(D.xs_g), 2 * p, nx, ny, t, Tf);
+      } else if (sub < 2) {
+        write_one_row<LC>(Z, static_cast<C*>(D.xs_phi), static_cast<C*>(D.xs_f), 2 * p + sub, nx, ny, t, Tf);
+        if (t == 0) static_cast<T*>(D.nyq_phi)[2 * p + sub] = Z[pad16(nx >> 1)].x;   // phi*'s row Nyquist
+      } else {
+        write_pair_rows<LC>(Z, static_cast<C*>(D.xs_w), 2 * p, nx, ny, t, Tf);
+        if (t == 0) {
+          const C zn = Z[pad16(nx >> 1)];
+          static_cast<T*>(D.nyq_omega)[2 * p] = zn.x;
+          static_cast<T*>(D.nyq_omega)[2 * p + 1] = zn.y;
+        }
+      }
+    }
+    __syncthreads();                                    // Z reads done before the next transform
   }
-  fft_reg<false>(vp, log2ny, t, buf, tw);
-  fft_reg<false>(vf, log2ny, t, buf, tw);
+  cp_async_wait_all();
+}
+
+// ============================================================ column passes
+// Work items: columns m = 0..nx/2-1, one column per instance (ny/8 threads).
+// The two input columns of the next item stream into the staging buffer while
+// the current one is transformed.  mode 0: phi (inputs phi*, f -> increment
+// of phi); mode 1: flow (g, omega* -> psi, increment of omega; Stokes: g ->
+// psi).
+template <class T>
+__device__ __forceinline__ void stage_column(cplx<T>* st, const cplx<T>* __restrict__ src, int m, int ny, int t,
+                                             int Tc) {
+  using C = cplx<T>;
+  constexpr int LC = Layout<T>::LC;
+  if (LC == 0) {
+    copy_async(st, src + (size_t)m * ny, ny * (int)sizeof(C), t, Tc);
+  } else {
+    for (int n = t; n < ny; n += Tc) cp_async8(st + n, src + xs_idx(n, m, ny, LC));
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(512, min_ctas<T>()) k_colpass(const MemberDesc* __restrict__ descs, int log2nx, int log2ny,
+                                                 const cplx<T>* __restrict__ tw, int mode) {
+  using C = cplx<T>;
+  constexpr int LC = Layout<T>::LC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const MemberDesc& D = descs[blockIdx.y];
+  const int nx = 1 << log2nx, ny = 1 << log2ny;
+  const int Tc = ny >> kLogP;
+  const int ipc = blockDim.x / Tc;
+  const int inst = threadIdx.x / Tc, t = threadIdx.x - inst * Tc;
+  const int nitems = nx >> 1;
+  const int stride = gridDim.x * ipc;
+  const bool stokes = D.stokes != 0;
+  const bool two = mode == 0 || !stokes;                // second input column
+  unsigned char* base = smem_raw + (size_t)inst * colpass_inst_bytes(ny, sizeof(T));
+  C* st0 = reinterpret_cast<C*>(base);
+  C* st1 = st0 + ny;
+  C* buf = st1 + ny;
+  C* in0 = static_cast<C*>(mode == 0 ? D.xs_phi : D.xs_g);
+  C* in1 = static_cast<C*>(mode == 0 ? D.xs_f : D.xs_w);
+
+  auto issue = [&](int m) {
+    if (m < nitems) {
+      stage_column<T>(st0, in0, m, ny, t, Tc);
+      if (two) stage_column<T>(st1, in1, m, ny, t, Tc);
+    }
+    cp_async_commit();
+  };
+
+  const T norm = (T)D.inv_nxny, qyu = (T)D.qy_unit;
+  const T caM = (T)D.c_dt_aM, cbM = (T)D.c_dt_bM, ckM = (T)D.c_hdt_kM;
+  const T cnu = (T)D.c_hdt_nu, dt = (T)D.dt;
   double s_d;
   long long K;
-  strain_dev(*D.n, D.gdot, D.dt, D.ratio, s_d, K);       // stage 1 uses s^n
-  const double qx_d = m * D.qx_unit;
-  const T qx = (T)qx_d;
-  const T sqx = (T)(s_d * qx_d);                          // s q_x formed in double
-  const T caM = (T)D.c_dt_aM, cbM = (T)D.c_dt_bM, ckM = (T)D.c_hdt_kM;
-  const T norm = (T)D.inv_nxny, qyu = (T)D.qy_unit;
+  strain_dev(*D.n + (mode == 0 ? 0 : 1), D.gdot, D.dt, D.ratio, s_d, K);   // s^n for phi, s^{n+1} for flow
+
+  const int iters = persistent_iters(nitems, ipc);
+  int m = blockIdx.x * ipc + inst;
+  issue(m);
+  for (int it = 0; it < iters; ++it, m += stride) {
+    const bool active = m < nitems;
+    cp_async_wait_all();
+    __syncthreads();
+    C va[kP], vb[kP];
+    const int mm = active ? m : 0;
 #pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const int nn = t + q * Tc;
-    C inc;
-    if (nn == (ny >> 1)) {
-      inc = C{-vp[q].x * norm, -vp[q].y * norm};          // Nyquist row of phi^{n+1} -> 0
-    } else {
+    for (int q = 0; q < kP; ++q) va[q] = st0[t + q * Tc];
+    if (two) {
+#pragma unroll
+      for (int q = 0; q < kP; ++q) vb[q] = st1[t + q * Tc];
+    }
+    __syncthreads();                                    // stage free
+    issue(m + stride);
+    fft_reg<false>(va, log2ny, t, buf, tw);
+    if (two) fft_reg<false>(vb, log2ny, t, buf, tw);
+    const double qx_d = mm * D.qx_unit;
+    const T qx = (T)qx_d;
+    const T sqx = (T)(s_d * qx_d);                      // s q_x formed in double
+#pragma unroll
+    for (int q = 0; q < kP; ++q) {
+      const int nn = t + q * Tc;
       const int ns = nn < (ny >> 1) ? nn : nn - ny;
       const T ky = (T)ns * qyu - sqx;
       const T k2 = qx * qx + ky * ky;
-      const T c4 = ckM * (k2 * k2);
-      const T a = caM * k2 - T(2) * c4;
-      const T b = cbM * k2;
-      const T inv = norm / (T(1) + c4);
-      inc = C{(a * vp[q].x - b * vf[q].x) * inv, (a * vp[q].y - b * vf[q].y) * inv};
+      const bool nyq_row = nn == (ny >> 1);
+      if (mode == 0) {
+        const C P = va[q], F = vb[q];
+        if (nyq_row) {
+          va[q] = C{-P.x * norm, -P.y * norm};          // Nyquist row of phi^{n+1} -> 0
+        } else {
+          const T c4 = ckM * (k2 * k2);
+          const T aa = caM * k2 - T(2) * c4;
+          const T bbm = cbM * k2;
+          const T inv = norm / (T(1) + c4);
+          va[q] = C{(aa * P.x - bbm * F.x) * inv, (aa * P.y - bbm * F.y) * inv};
+        }
+      } else {
+        const bool zero = nyq_row || (mm == 0 && nn == 0);
+        const C G = va[q];
+        if (stokes) {
+          const T inv = zero ? T(0) : norm / (k2 * k2);
+          va[q] = C{G.x * inv, G.y * inv};
+        } else {
+          const C Wv = vb[q];
+          if (zero) {
+            va[q] = C{T(0), T(0)};
+            vb[q] = C{-Wv.x * norm, -Wv.y * norm};      // omega^{n+1} -> 0 there
+          } else {
+            const T cc = cnu * k2;
+            const T inv = T(1) / (T(1) + cc);
+            const C dw = C{(-T(2) * cc * Wv.x + dt * G.x) * inv, (-T(2) * cc * Wv.y + dt * G.y) * inv};
+            const T ik = norm / k2;
+            va[q] = C{(Wv.x + dw.x) * ik, (Wv.y + dw.y) * ik};
+            vb[q] = C{dw.x * norm, dw.y * norm};
+          }
+        }
+      }
     }
-    vp[q] = inc;
-  }
-  fft_reg<true>(vp, log2ny, t, buf, tw);
+    fft_reg<true>(va, log2ny, t, buf, tw);
+    if (active) {
 #pragma unroll
-  for (int q = 0; q < 16; ++q) xp[xs_idx(t + q * Tc, m, ny, LC)] = vp[q];
+      for (int q = 0; q < kP; ++q) in0[xs_idx(t + q * Tc, m, ny, LC)] = va[q];
+    }
+    if (mode == 1 && !stokes) {
+      fft_reg<true>(vb, log2ny, t, buf, tw);
+      if (active) {
+#pragma unroll
+        for (int q = 0; q < kP; ++q) in1[xs_idx(t + q * Tc, m, ny, LC)] = vb[q];
+      }
+    }
+  }
+  cp_async_wait_all();
 }
 
+// ====================================================== inverse row transforms
+// Work items: mode 0 (phi): row pairs of the phi increment; mode 1 (flow): per
+// row pair, item 0 = psi, item 1 = the omega increment (inertial members).  The
+// item's 32-byte chunks stream into the staging buffer during the previous
+// transform; Z[k] = A[k] + i B[k], Z[N-k] = conj A[k] + i conj B[k] (A, B the
+// two rows), Z[0] from the real parts, Z[N/2] = minus the staged field's row
+// Nyquist coefficients / nx.
 template <class T>
-__global__ void __launch_bounds__(col_threads<T>()) k_colpass_flow(const MemberDesc* __restrict__ descs, int log2nx,
-                                                       int log2ny, int log2nc, const cplx<T>* __restrict__ tw) {
+__global__ void __launch_bounds__(512, min_ctas<T>()) k_rowinv(const MemberDesc* __restrict__ descs, int log2nx, int log2ny,
+                                                const cplx<T>* __restrict__ tw, int mode) {
   using C = cplx<T>;
   constexpr int LC = Layout<T>::LC;
+  constexpr int CL = 1 << LC;
+  constexpr int H = 16 / sizeof(C);                     // complex values per 16 bytes
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const MemberDesc& D = descs[blockIdx.y];
-  const int ny = 1 << log2ny;
-  const int Tc = ny >> 4;
-  const int c = threadIdx.x & ((1 << log2nc) - 1), t = threadIdx.x >> log2nc;
-  const int m = (blockIdx.x << log2nc) + c;
-  C* buf = reinterpret_cast<C*>(smem_raw) + (size_t)c * padded_len(ny);
-  C* xg = static_cast<C*>(D.xs_g);
-  C* xw = static_cast<C*>(D.xs_w);
-  const bool stokes = D.stokes != 0;
-  C vg[16], vw[16];
-#pragma unroll
-  for (int q = 0; q < 16; ++q) vg[q] = xg[xs_idx(t + q * Tc, m, ny, LC)];
-  if (!stokes) {
-#pragma unroll
-    for (int q = 0; q < 16; ++q) vw[q] = xw[xs_idx(t + q * Tc, m, ny, LC)];
-  }
-  fft_reg<false>(vg, log2ny, t, buf, tw);
-  if (!stokes) fft_reg<false>(vw, log2ny, t, buf, tw);
-  double s_d;
-  long long K;
-  strain_dev(*D.n + 1, D.gdot, D.dt, D.ratio, s_d, K);   // stages 2-3 use s^{n+1}
-  const double qx_d = m * D.qx_unit;
-  const T qx = (T)qx_d;
-  const T sqx = (T)(s_d * qx_d);
-  const T norm = (T)D.inv_nxny, qyu = (T)D.qy_unit;
-  const T cnu = (T)D.c_hdt_nu, dt = (T)D.dt;
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const int nn = t + q * Tc;
-    const bool zero = (nn == (ny >> 1)) || (m == 0 && nn == 0);
-    const int ns = nn < (ny >> 1) ? nn : nn - ny;
-    const T ky = (T)ns * qyu - sqx;
-    const T k2 = qx * qx + ky * ky;
-    const C G = vg[q];
-    if (stokes) {
-      const T inv = zero ? T(0) : norm / (k2 * k2);
-      vg[q] = C{G.x * inv, G.y * inv};
-    } else {
-      const C W = vw[q];
-      C inc, ps;
-      if (zero) {
-        inc = C{-W.x * norm, -W.y * norm};                 // omega^{n+1} -> 0 there
-        ps = C{T(0), T(0)};
-      } else {
-        const T cc = cnu * k2;
-        const T inv = T(1) / (T(1) + cc);
-        const C dw = C{(-T(2) * cc * W.x + dt * G.x) * inv, (-T(2) * cc * W.y + dt * G.y) * inv};
-        const T ik = norm / k2;
-        ps = C{(W.x + dw.x) * ik, (W.y + dw.y) * ik};
-        inc = C{dw.x * norm, dw.y * norm};
-      }
-      vg[q] = ps;
-      vw[q] = inc;
-    }
-  }
-  fft_reg<true>(vg, log2ny, t, buf, tw);
-#pragma unroll
-  for (int q = 0; q < 16; ++q) xg[xs_idx(t + q * Tc, m, ny, LC)] = vg[q];
-  if (!stokes) {
-    fft_reg<true>(vw, log2ny, t, buf, tw);
-#pragma unroll
-    for (int q = 0; q < 16; ++q) xw[xs_idx(t + q * Tc, m, ny, LC)] = vw[q];
-  }
-}
-
-// ----------------------------------------------------------- inverse rows
-// Z for the inverse row transform of rows (j0, j0+1) of one x-spectral field:
-// Z[k] = A[k] + i B[k] (0 < k < N/2), Z[0] = Re A[0] + i Re B[0], Z[N/2] = zn,
-// Z[N-k] = conj A[k] + i conj B[k] (A = row j0, B = row j0+1).  Each thread
-// loads whole 32-byte chunks (both rows of CL modes) and scatters them into the
-// padded buffer; a barrier follows.
-template <int LC, class C>
-__device__ __forceinline__ void load_pair_rows_to_smem(C* Z, const C* __restrict__ xs, int j0, C zn, int nx,
-                                                       int ny, int t, int Tthreads) {
-  constexpr int CL = 1 << LC;
+  const int nx = 1 << log2nx, ny = 1 << log2ny, mx = nx - 1;
+  const int Tf = nx >> kLogP;
+  const int ipc = blockDim.x / Tf;
+  const int inst = threadIdx.x / Tf, t = threadIdx.x - inst * Tf;
+  const int nsub = (mode == 1 && !D.stokes) ? 2 : 1;
+  const int nitems = (ny >> 1) * nsub;
+  const int stride = gridDim.x * ipc;
   const int nchunk = (nx >> 1) >> LC;
-  for (int cb = t; cb < nchunk; cb += Tthreads) {
-    const float4* p4 = reinterpret_cast<const float4*>(xs + ((((size_t)cb * ny) + j0) << LC));
-    union { float4 f4[2]; C c[2 * CL]; } u;
-    u.f4[0] = __ldg(p4);
-    u.f4[1] = __ldg(p4 + 1);
-#pragma unroll
-    for (int c = 0; c < CL; ++c) {
-      const int k = (cb << LC) + c;
-      const C A = u.c[c], B = u.c[CL + c];
-      if (k == 0) {
-        Z[pad16(0)] = C{A.x, B.x};
-        Z[pad16(nx >> 1)] = zn;
-      } else {
-        Z[pad16(k)] = C{A.x - B.y, A.y + B.x};
-        Z[pad16(nx - k)] = C{A.x + B.y, B.x - A.y};
+  unsigned char* base = smem_raw + (size_t)inst * rowinv_inst_bytes(nx, sizeof(T));
+  C* stage = reinterpret_cast<C*>(base);               // chunk cb at stage[2 CL cb]
+  C* Z = stage + nx;
+
+  auto issue = [&](int w) {
+    if (w < nitems) {
+      const int sub = w % nsub;
+      const C* src = static_cast<const C*>(mode == 0 ? D.xs_phi : (sub == 0 ? D.xs_g : D.xs_w));
+      const int j0 = 2 * (w / nsub);
+      for (int cb = t; cb < nchunk; cb += Tf) {
+        const C* g = src + ((((size_t)cb * ny) + j0) << LC);
+        cp_async16(stage + 2 * CL * cb, g);
+        cp_async16(stage + 2 * CL * cb + H, g + H);
       }
     }
-  }
-  __syncthreads();
-}
+    cp_async_commit();
+  };
 
-// Chunks of a row pair held in registers between their load and their scatter
-// into Z: thread t holds chunks cb = t + Tf u, u < NCH, each 32 bytes (rows
-// j0 and j0+1 of CL modes).
-template <class C, int LC>
-struct PairChunks {
-  static constexpr int NCH = 8 >> LC;               // (nx/2 / CL) / (nx/16)
-  float4 f4[NCH][2];
-  __device__ __forceinline__ void load(const C* __restrict__ xs, int j0, int ny, int t, int Tf) {
-#pragma unroll
-    for (int u = 0; u < NCH; ++u) {
-      const int cb = t + u * Tf;
-      const float4* p4 = reinterpret_cast<const float4*>(xs + ((((size_t)cb * ny) + j0) << LC));
-      f4[u][0] = __ldg(p4);
-      f4[u][1] = __ldg(p4 + 1);
-    }
+  long long dK = 0;
+  if (mode == 0 && D.remap) {
+    double s0, s1;
+    long long K0, K1;
+    const long long n = *D.n;
+    strain_dev(n, D.gdot, D.dt, D.ratio, s0, K0);
+    strain_dev(n + 1, D.gdot, D.dt, D.ratio, s1, K1);
+    dK = K1 - K0;
   }
-  // Z[k] = A[k] + i B[k], Z[N-k] = conj A[k] + i conj B[k], Z[0] real parts,
-  // Z[N/2] = zn; followed by a barrier
-  __device__ __forceinline__ void scatter(C* Z, C zn, int nx, int t, int Tf) const {
-    constexpr int CL = 1 << LC;
-#pragma unroll
-    for (int u = 0; u < NCH; ++u) {
-      union { float4 f[2]; C c[2 * CL]; } w;
-      w.f[0] = f4[u][0];
-      w.f[1] = f4[u][1];
-      const int cb = t + u * Tf;
+  const T rn = T(1) / T(nx);
+  const int iters = persistent_iters(nitems, ipc);
+  int w = blockIdx.x * ipc + inst;
+  issue(w);
+  for (int it = 0; it < iters; ++it, w += stride) {
+    const bool active = w < nitems;
+    const int p = w / nsub, sub = w - p * nsub;
+    const int j0 = 2 * p, j1 = j0 + 1;
+    const int kind = mode == 0 ? 0 : (sub == 0 ? 1 : 2);   // phi increment, psi, omega increment
+    C zn = C{T(0), T(0)};
+    if (active && kind != 1) {
+      const T* nq = static_cast<const T*>(kind == 0 ? D.nyq_phi : D.nyq_omega);
+      zn = C{-nq[j0] * rn, -nq[j1] * rn};
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int cb = t; cb < nchunk; cb += Tf) {
 #pragma unroll
       for (int c = 0; c < CL; ++c) {
         const int k = (cb << LC) + c;
-        const C A = w.c[c], B = w.c[CL + c];
+        const C A = stage[2 * CL * cb + c], B = stage[2 * CL * cb + CL + c];
         if (k == 0) {
           Z[pad16(0)] = C{A.x, B.x};
           Z[pad16(nx >> 1)] = zn;
@@ -533,266 +572,117 @@ struct PairChunks {
         }
       }
     }
-    __syncthreads();
-  }
-};
-
-// phi^{n+1} rows (j0, j1) = phi* + increment - phi*'s row Nyquist component,
-// written at the remapped positions when the strain wraps during this step.
-// Persistent: each instance walks row pairs with a stride of all instances of
-// the grid and loads the next pair's spectrum while transforming the current.
-template <class T>
-__global__ void __launch_bounds__(256, min_ctas<T>(2, 1)) k_rowinv_phi(const MemberDesc* __restrict__ descs,
-                                                                        int log2nx, int log2ny,
-                                                                        const cplx<T>* __restrict__ tw) {
-  using C = cplx<T>;
-  constexpr int LC = Layout<T>::LC;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const MemberDesc& D = descs[blockIdx.y];
-  const int nx = 1 << log2nx, ny = 1 << log2ny, mx = nx - 1;
-  const int Tf = nx >> 4;
-  const int ipc = blockDim.x / Tf;
-  const int inst = threadIdx.x / Tf, t = threadIdx.x - inst * Tf;
-  const int npairs = ny >> 1;
-  const int stride = gridDim.x * ipc;
-  C* Z = reinterpret_cast<C*>(smem_raw) + (size_t)inst * padded_len(nx);
-  long long dK = 0;
-  if (D.remap) {
-    double s0, s1;
-    long long K0, K1;
-    const long long n = *D.n;
-    strain_dev(n, D.gdot, D.dt, D.ratio, s0, K0);
-    strain_dev(n + 1, D.gdot, D.dt, D.ratio, s1, K1);
-    dK = K1 - K0;
-  }
-  const T* nq = static_cast<const T*>(D.nyq_phi);
-  const T rn = T(1) / T(nx);
-  const C* xp = static_cast<const C*>(D.xs_phi);
-  const T* phis = static_cast<const T*>(D.phi_star);
-  T* phi = static_cast<T*>(D.phi);
-  // every instance of the CTA runs the same number of iterations (barriers)
-  const int iters = (npairs - (int)blockIdx.x * ipc + stride - 1) / stride;
-  int pair = blockIdx.x * ipc + inst;
-  PairChunks<C, LC> ch;
-  if (pair < npairs) ch.load(xp, 2 * pair, ny, t, Tf);
-  for (int it = 0; it < iters; ++it) {
-    const bool active = pair < npairs;
-    const int j0 = 2 * pair, j1 = j0 + 1;
-    C zn = C{T(0), T(0)};
-    if (active) zn = C{-nq[j0] * rn, -nq[j1] * rn};
-    if (active) ch.scatter(Z, zn, nx, t, Tf);
-    else __syncthreads();
-    C v[16];
+    __syncthreads();                                    // Z complete, stage free
+    issue(w + stride);
+    C v[kP];
     smem_to_reg(v, Z, log2nx, t);
-    __syncthreads();                                // Z becomes the exchange buffer
-    const int next = pair + stride;
-    if (next < npairs) ch.load(xp, 2 * next, ny, t, Tf);   // in flight during the FFT
-    T ps0[16], ps1[16];
-    if (active) {
+    __syncthreads();                                    // Z becomes the exchange buffer
+    // the real-space base of the increment (phi* or omega*), loaded before the transform
+    T b0[kP], b1[kP];
+    if (active && kind != 1) {
+      const T* bs = static_cast<const T*>(kind == 0 ? D.phi_star : D.omega_star);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int i = t + q * Tf;
-        ps0[q] = phis[((size_t)j0 << log2nx) + i];
-        ps1[q] = phis[((size_t)j1 << log2nx) + i];
+      for (int q = 0; q < kP; ++q) {
+        b0[q] = bs[((size_t)j0 << log2nx) + t + q * Tf];
+        b1[q] = bs[((size_t)j1 << log2nx) + t + q * Tf];
       }
     }
     fft_reg<true>(v, log2nx, t, Z, tw);
     if (active) {
-      const int sh0 = dK ? remap_shift(dK, D.ratio, j0, nx) : 0;
-      const int sh1 = dK ? remap_shift(dK, D.ratio, j1, nx) : 0;
+      if (kind == 1) {
+        T* out = static_cast<T*>(D.psi);
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int i = t + q * Tf;
-        phi[((size_t)j0 << log2nx) + ((i + sh0) & mx)] = ps0[q] + v[q].x;
-        phi[((size_t)j1 << log2nx) + ((i + sh1) & mx)] = ps1[q] + v[q].y;
+        for (int q = 0; q < kP; ++q) {
+          out[((size_t)j0 << log2nx) + t + q * Tf] = v[q].x;
+          out[((size_t)j1 << log2nx) + t + q * Tf] = v[q].y;
+        }
+      } else {
+        T* out = static_cast<T*>(kind == 0 ? D.phi : D.omega);
+        const int sh0 = (kind == 0 && dK) ? remap_shift(dK, D.ratio, j0, nx) : 0;
+        const int sh1 = (kind == 0 && dK) ? remap_shift(dK, D.ratio, j1, nx) : 0;
+#pragma unroll
+        for (int q = 0; q < kP; ++q) {
+          const int i = t + q * Tf;
+          out[((size_t)j0 << log2nx) + ((i + sh0) & mx)] = b0[q] + v[q].x;
+          out[((size_t)j1 << log2nx) + ((i + sh1) & mx)] = b1[q] + v[q].y;
+        }
       }
     }
-    __syncthreads();                                // last exchange reads done before the next scatter
-    pair = next;
   }
-}
-
-// psi rows (j0, j1) from psi_hat; for inertial members also omega^{n+1} =
-// omega* + increment - omega*'s row Nyquist component.  Advances n.
-template <class T>
-__global__ void __launch_bounds__(256, min_ctas<T>(2, 1)) k_rowinv_flow(const MemberDesc* __restrict__ descs,
-                                                                         int log2nx, int log2ny,
-                                                                         const cplx<T>* __restrict__ tw) {
-  using C = cplx<T>;
-  constexpr int LC = Layout<T>::LC;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const MemberDesc& D = descs[blockIdx.y];
-  const int nx = 1 << log2nx, ny = 1 << log2ny;
-  const int Tf = nx >> 4;
-  const int inst = threadIdx.x / Tf, t = threadIdx.x - inst * Tf;
-  const int j0 = 2 * (blockIdx.x * (blockDim.x / Tf) + inst), j1 = j0 + 1;
-  C* Z = reinterpret_cast<C*>(smem_raw) + (size_t)inst * padded_len(nx);
-  T* psi = static_cast<T*>(D.psi);
-  C v[16];
-  load_pair_rows_to_smem<LC>(Z, static_cast<const C*>(D.xs_g), j0, C{T(0), T(0)}, nx, ny, t, Tf);
-  smem_to_reg(v, Z, log2nx, t);
-  __syncthreads();
-  fft_reg<true>(v, log2nx, t, Z, tw);
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    const int i = t + q * Tf;
-    psi[((size_t)j0 << log2nx) + i] = v[q].x;
-    psi[((size_t)j1 << log2nx) + i] = v[q].y;
-  }
-  if (!D.stokes) {
-    __syncthreads();                                // last exchange reads of Z are done
-    const T* nq = static_cast<const T*>(D.nyq_omega);
-    const T rn = T(1) / T(nx);
-    load_pair_rows_to_smem<LC>(Z, static_cast<const C*>(D.xs_w), j0, C{-nq[j0] * rn, -nq[j1] * rn}, nx, ny, t,
-                               Tf);
-    smem_to_reg(v, Z, log2nx, t);
-    __syncthreads();
-    fft_reg<true>(v, log2nx, t, Z, tw);
-    const T* oms = static_cast<const T*>(D.omega_star);
-    T* om = static_cast<T*>(D.omega);
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const int i = t + q * Tf;
-      om[((size_t)j0 << log2nx) + i] = oms[((size_t)j0 << log2nx) + i] + v[q].x;
-      om[((size_t)j1 << log2nx) + i] = oms[((size_t)j1 << log2nx) + i] + v[q].y;
-    }
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) *D.n += 1;
-}
-
-// ----------------------------------------------------------------- stage 2
-// One instance = rows (j0, j1); per chunk q of Tf points the phi tile (6 rows
-// j0-2..j1+2, Tf + 6 columns) is staged by cp.async one chunk ahead, mu is
-// computed on 4 rows x (Tf + 4) columns into shared memory, then g for both
-// rows.  One FFT of (g_j0 + i g_j1).
-template <class T>
-__global__ void __launch_bounds__(256, min_ctas<T>(3, 1)) k_stage2(const MemberDesc* __restrict__ descs, int log2nx,
-                                                                    int log2ny, const cplx<T>* __restrict__ tw) {
-  using C = cplx<T>;
-  constexpr int LC = Layout<T>::LC;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const MemberDesc& D = descs[blockIdx.y];
-  const int nx = 1 << log2nx, ny = 1 << log2ny, mx = nx - 1, my = ny - 1;
-  const int Tf = nx >> 4;
-  const int inst = threadIdx.x / Tf, t = threadIdx.x - inst * Tf;
-  const int j0 = 2 * (blockIdx.x * (blockDim.x / Tf) + inst);
-  const int W = Tf + 4, W2 = Tf + 6;
-  unsigned char* base = smem_raw + (size_t)inst * stage2_inst_bytes(nx, sizeof(T));
-  C* Z = reinterpret_cast<C*>(base);
-  T* ptile = reinterpret_cast<T*>(base + (size_t)padded_len(nx) * sizeof(C));   // 2 x 6 x W2
-  T* mt = ptile + 2 * 6 * W2;                                                   // 4 x W
-
-  double s_d;
-  long long K;
-  strain_dev(*D.n + 1, D.gdot, D.dt, D.ratio, s_d, K);   // s^{n+1}
-  const T s = (T)s_d;
-  const T w1 = (s < T(0) ? -s : s) * T(0.5);
-  const T w0 = T(1) - w1;
-  const int d = s >= T(0) ? -2 : 2;
-  const T a = (T)D.a, b = (T)D.b, kappa = (T)D.kappa;
-  const T inv2h = (T)D.inv_2h, ih2 = (T)D.inv_h2, i4h2 = (T)D.inv_4h2;
-  const T cxx = T(1) + s * s, cxy = T(2) * s;
-  const T cf = (T)D.c_force;
-  const T* fld[1] = {static_cast<const T*>(D.phi)};
-
-  C v[16];
-  load_tile_async<T, 1>(ptile, fld, j0 - 2, 6, -3, W2, mx, my, log2nx, t, Tf);
-  cp_async_commit();
-#pragma unroll
-  for (int q = 0; q < 16; ++q) {
-    if (q + 1 < 16) {
-      load_tile_async<T, 1>(ptile + ((q + 1) & 1) * 6 * W2, fld, j0 - 2, 6, Tf * (q + 1) - 3, W2, mx, my, log2nx, t,
-                            Tf);
-      cp_async_commit();
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    __syncthreads();
-    const T* pt = ptile + (q & 1) * 6 * W2;
-    // mu (Appendix B item 2) on tile rows 1..4 (j0-1..j1+1), columns 1..W2-2
-    for (int r = 0; r < 4; ++r) {
-      for (int x = t; x < W; x += Tf) {
-        const int pr = r + 1, px = x + 1;
-        const T pc = pt[pr * W2 + px];
-        const T dxx = (pt[pr * W2 + px + 1] - T(2) * pc + pt[pr * W2 + px - 1]) * ih2;
-        const T dyy = (pt[(pr + 1) * W2 + px] - T(2) * pc + pt[(pr - 1) * W2 + px]) * ih2;
-        const T dxy = (pt[(pr + 1) * W2 + px + 1] - pt[(pr - 1) * W2 + px + 1] - pt[(pr + 1) * W2 + px - 1] +
-                       pt[(pr - 1) * W2 + px - 1]) * i4h2;
-        const T lap = cxx * dxx - cxy * dxy + dyy;
-        mt[r * W + x] = -a * pc + b * ((pc * pc) * pc) - kappa * lap;
-      }
-    }
-    __syncthreads();
-    T g[2];
-#pragma unroll
-    for (int jj = 0; jj < 2; ++jj) {
-      const int rp = jj + 2, rm = jj + 1;           // phi tile row, mu tile row of j0 + jj
-      const int xp = t + 3, xm = t + 2;
-      const T dxphi = tile_dx(pt, rp, xp, W2, inv2h);
-      const T dyphi = tile_dy(pt, rp, xp, W2, w0, w1, d, inv2h);
-      const T dxmu = tile_dx(mt, rm, xm, W, inv2h);
-      const T dymu = tile_dy(mt, rm, xm, W, w0, w1, d, inv2h);
-      g[jj] = cf * (dxphi * dymu - dyphi * dxmu);
-    }
-    v[q] = C{g[0], g[1]};
-    __syncthreads();                                // tiles may now be refilled
-  }
-  fft_reg<false>(v, log2nx, t, Z, tw);
-  reg_to_smem(v, log2nx, t, Z);
-  write_pair_rows<LC>(Z, Z, true, static_cast<C*>(D.xs_g), static_cast<C*>(nullptr), j0, nx, ny, t, Tf);
+  cp_async_wait_all();
+  if (mode == 1 && blockIdx.x == 0 && threadIdx.x == 0) *D.n += 1;
 }
 
 // ----------------------------------------------------------------- launchers
 template <class T>
-void launch_stage1(const MemberDesc* d, int nmem, int log2nx, int log2ny, const cplx<T>* tw, const RowCfg& c,
-                   cudaStream_t st) {
-  k_stage1<T><<<dim3(c.ctas, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw);
+void launch_step_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int log2ny, const cplx<T>* tw,
+                        const LaunchCfg& c, cudaStream_t st) {
+  switch (kind) {
+    case KIND_STENCIL1:
+      switch (log2nx) {
+        case 4: k_stencil1<T, 16><<<dim3(c.grid_x, c.grid_y, nmem), c.threads, 0, st>>>(d, log2nx, log2ny); break;
+        case 5: k_stencil1<T, 32><<<dim3(c.grid_x, c.grid_y, nmem), c.threads, 0, st>>>(d, log2nx, log2ny); break;
+        case 6: k_stencil1<T, 64><<<dim3(c.grid_x, c.grid_y, nmem), c.threads, 0, st>>>(d, log2nx, log2ny); break;
+        default: k_stencil1<T, 128><<<dim3(c.grid_x, c.grid_y, nmem), c.threads, 0, st>>>(d, log2nx, log2ny); break;
+      }
+      break;
+    case KIND_ROWFWD_PHI:
+      k_rowfwd<T><<<dim3(c.grid_x, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw, 0);
+      break;
+    case KIND_COLPASS_PHI:
+      k_colpass<T><<<dim3(c.grid_x, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw, 0);
+      break;
+    case KIND_ROWINV_PHI:
+      k_rowinv<T><<<dim3(c.grid_x, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw, 0);
+      break;
+    case KIND_STENCIL2:
+      switch (log2nx) {
+        case 4: k_stencil2<T, 16><<<dim3(c.grid_x, c.grid_y, nmem), c.threads, 0, st>>>(d, log2nx, log2ny); break;
+        case 5: k_stencil2<T, 32><<<dim3(c.grid_x, c.grid_y, nmem), c.threads, 0, st>>>(d, log2nx, log2ny); break;
+        case 6: k_stencil2<T, 64><<<dim3(c.grid_x, c.grid_y, nmem), c.threads, 0, st>>>(d, log2nx, log2ny); break;
+        default: k_stencil2<T, 128><<<dim3(c.grid_x, c.grid_y, nmem), c.threads, 0, st>>>(d, log2nx, log2ny); break;
+      }
+      break;
+    case KIND_ROWFWD_G:
+      k_rowfwd<T><<<dim3(c.grid_x, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw, 1);
+      break;
+    case KIND_COLPASS_FLOW:
+      k_colpass<T><<<dim3(c.grid_x, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw, 1);
+      break;
+    default:
+      k_rowinv<T><<<dim3(c.grid_x, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw, 1);
+      break;
+  }
 }
+
+// CTAs of a persistent kind that fit on one SM at (threads, smem)
 template <class T>
-void launch_colpass_phi(const MemberDesc* d, int nmem, int log2nx, int log2ny, const cplx<T>* tw,
-                        const ColCfg& c, cudaStream_t st) {
-  k_colpass_phi<T><<<dim3(c.ctas, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, c.log2cols, tw);
-}
-template <class T>
-void launch_rowinv(const MemberDesc* d, int nmem, int log2nx, int log2ny, const cplx<T>* tw, const RowCfg& c,
-                   int mode, cudaStream_t st) {
-  if (mode == 0) k_rowinv_phi<T><<<dim3(c.ctas, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw);
-  else k_rowinv_flow<T><<<dim3(c.ctas, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw);
-}
-template <class T>
-void launch_stage2(const MemberDesc* d, int nmem, int log2nx, int log2ny, const cplx<T>* tw, const RowCfg& c,
-                   cudaStream_t st) {
-  k_stage2<T><<<dim3(c.ctas, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw);
-}
-template <class T>
-void launch_colpass_flow(const MemberDesc* d, int nmem, int log2nx, int log2ny, const cplx<T>* tw,
-                         const ColCfg& c, cudaStream_t st) {
-  k_colpass_flow<T><<<dim3(c.ctas, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, c.log2cols, tw);
+int step_kernel_occupancy(int kind, int threads, size_t smem) {
+  int nb = 0;
+  const void* f = nullptr;
+  switch (kind) {
+    case KIND_ROWFWD_PHI:
+    case KIND_ROWFWD_G: f = (const void*)k_rowfwd<T>; break;
+    case KIND_COLPASS_PHI:
+    case KIND_COLPASS_FLOW: f = (const void*)k_colpass<T>; break;
+    default: f = (const void*)k_rowinv<T>; break;
+  }
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads, smem) != cudaSuccess) nb = 1;
+  return nb < 1 ? 1 : nb;
 }
 
 template <class T>
 void set_step_smem_limits() {
   const int lim = 220 * 1024;   // dynamic part; leaves room for static shared memory
-  cudaFuncSetAttribute(k_stage1<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_colpass_phi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_colpass_flow<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_rowinv_phi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_rowinv_flow<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-  cudaFuncSetAttribute(k_stage2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_rowfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_colpass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_rowinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
-#define SHF_INST(T)                                                                                       \
-  template void launch_stage1<T>(const MemberDesc*, int, int, int, const cplx<T>*, const RowCfg&,          \
-                                 cudaStream_t);                                                            \
-  template void launch_colpass_phi<T>(const MemberDesc*, int, int, int, const cplx<T>*, const ColCfg&,     \
-                                      cudaStream_t);                                                       \
-  template void launch_rowinv<T>(const MemberDesc*, int, int, int, const cplx<T>*, const RowCfg&, int,     \
-                                 cudaStream_t);                                                            \
-  template void launch_stage2<T>(const MemberDesc*, int, int, int, const cplx<T>*, const RowCfg&,          \
-                                 cudaStream_t);                                                            \
-  template void launch_colpass_flow<T>(const MemberDesc*, int, int, int, const cplx<T>*, const ColCfg&,    \
-                                       cudaStream_t);                                                      \
+#define SHF_INST(T)                                                                                      \
+  template void launch_step_kernel<T>(int, const MemberDesc*, int, int, int, const cplx<T>*,             \
+                                      const LaunchCfg&, cudaStream_t);                                    \
+  template int step_kernel_occupancy<T>(int, int, size_t);                                                \
   template void set_step_smem_limits<T>();
 
 SHF_INST(float)
