@@ -173,6 +173,29 @@ int shf_ensemble_member(shf_grid* ens, int r, shf_grid** view);
 int shf_strain(int64_t n, double gdot, double dt, int nx, int ny, double* s, int64_t* wraps);
 int shf_noise_fill(double* out, int64_t count, uint64_t seed, double amp);
 
+/* Mean of a caller-owned device field, like shf_mass, for callers that cannot
+ * let the library allocate device memory.  The paper has no counterpart: this
+ * is a service entry point, not a step of the method.
+ *   d_field: device pointer (or managed) to ny*nx reals of the given
+ *     precision (SHF_FP32 or SHF_FP64), row-major, element-aligned; only read.
+ *   nx, ny: 1..4096 each (any sizes, not only grid sizes); larger fields are
+ *     rejected with SHF_EINVAL before any device work.
+ *   cuda_stream: cudaStream_t to run on (NULL: the legacy default stream); the
+ *     call synchronises it before returning.
+ *   mean_phi: receives the mean (NaN on any error).
+ * Same reductions as shf_mass (1024-CTA Neumaier partials folded in CTA
+ * order), so for the same field both return the same bits.  Allocates
+ * nothing: the partials live in a fixed 24,600-byte device array of the
+ * library (one per device), found with cudaGetSymbolAddress on each call.
+ * That array is shared by all calls on a device, so calls that overlap in
+ * time on one device (from several host threads) race and must be serialised
+ * by the caller; calls from one thread never overlap, since each returns only
+ * after its stream has drained.  Returns SHF_EINVAL for NULL pointers, a bad
+ * precision, sizes out of range, a misaligned or host pointer; SHF_ECUDA for
+ * a CUDA failure; SHF_ENONFINITE (mean NaN) if the field holds NaN or Inf.
+ * No grid is involved, so shf_last_error has no message for it. */
+int shf_mass_static(const void* d_field, int precision, int nx, int ny, void* cuda_stream, double* mean_phi);
+
 #ifdef __cplusplus
 }
 #endif

@@ -85,6 +85,15 @@ def shf_noise_fill(count, seed, amp):
     return out
 
 
+def shf_mass_static(d_field, precision, nx, ny, stream=None):
+    """Mean of a device field (pointer or tensor) without device allocation."""
+    ptr = int(d_field.data_ptr()) if hasattr(d_field, "data_ptr") else d_field
+    m = ctypes.c_double()
+    _check(lib().shf_mass_static(ptr, int(precision), int(nx), int(ny), _stream_handle(stream),
+                                 ctypes.byref(m)), what="shf_mass_static")
+    return m.value
+
+
 def shf_create_grid(nx, ny, dx=1.0, precision=SHF_FP32, remap_mode=SHF_REMAP_SHIFT, stream=None):
     h = ctypes.c_void_p()
     _check(lib().shf_create_grid(ctypes.byref(h), int(nx), int(ny), float(dx), int(precision),
