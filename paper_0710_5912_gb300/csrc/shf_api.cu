@@ -1,5 +1,5 @@
 // Host side of the C ABI declared in include/shf.h: grid and ensemble objects,
-// device memory, launch configuration, per-step orchestration (six launches
+// device memory, launch configuration, per-step orchestration (eight launches
 // per step and size class; runs of 100 steps are replayed from a captured CUDA
 // graph), conversions, diagnostics and checkpoints.
 #include <cmath>
@@ -34,7 +34,7 @@ struct Member {
   void* phi_star = nullptr;
   void* omega_star = nullptr;
   void* nyq = nullptr;        // 2 ny reals: nyq_phi then nyq_omega
-  long long* d_n = nullptr;   // into the owner's counter array
+  StepState* d_st = nullptr;  // into the owner's step-state array
   int cls = -1, slot = -1;
 };
 
@@ -68,7 +68,7 @@ struct shf_grid {
   bool own_stream = false;
   std::vector<Member> members;
   std::vector<SizeClass> classes;
-  long long* d_counters = nullptr;
+  StepState* d_state = nullptr;   // per member: counter and strain of the current step
   long long n = 0;
   void* d_tw = nullptr;     // W[k] = exp(2 pi i k / NMAX) (shared-memory FFTs of the diagnostics)
   void* d_twr = nullptr;    // per-stage tables of the register FFT (step kernels)
@@ -237,7 +237,7 @@ MemberDesc make_desc(const shf_grid* o, const Member& m) {
   d.nyq_phi = m.nyq;
   d.nyq_omega = static_cast<char*>(m.nyq) + (size_t)m.ny * (o->precision == SHF_FP64 ? 8 : 4);
   d.gbuf = m.phi_star;   // g is formed after phi^{n+1}, when phi* is no longer needed
-  d.n = m.d_n;
+  d.st = m.d_st;
   d.a = m.a; d.b = m.b; d.kappa = m.kappa; d.M = m.M; d.eta = m.eta; d.rho = m.rho;
   d.gdot = m.gdot; d.dt = m.dt; d.dx = m.dx;
   d.c_dt_aM = (m.dt * m.a) * m.M;
@@ -319,7 +319,7 @@ void free_all(shf_grid* g) {
     cudaFree(m.nyq);
   }
   for (auto& cl : g->classes) cudaFree(cl.d_desc);
-  cudaFree(g->d_counters);
+  cudaFree(g->d_state);
   cudaFree(g->d_tw);
   cudaFree(g->d_twr);
   cudaFree(g->d_stage);
@@ -366,9 +366,9 @@ int build(shf_grid* g, const std::vector<int>& nx, const std::vector<int>& ny, c
   SHF_CUDA(g, cudaGetLastError());
   const int nm = (int)nx.size();
   g->members.resize(nm);
-  if (cudaMalloc(&g->d_counters, nm * sizeof(long long)) != cudaSuccess)
+  if (cudaMalloc(&g->d_state, nm * sizeof(StepState)) != cudaSuccess)
     return fail(g, SHF_ENOMEM, "counter allocation failed");
-  SHF_CUDA(g, cudaMemsetAsync(g->d_counters, 0, nm * sizeof(long long), g->stream));
+  SHF_CUDA(g, cudaMemsetAsync(g->d_state, 0, nm * sizeof(StepState), g->stream));
   const size_t R = real_size(g);
   for (int r = 0; r < nm; ++r) {
     Member& m = g->members[r];
@@ -377,7 +377,7 @@ int build(shf_grid* g, const std::vector<int>& nx, const std::vector<int>& ny, c
     m.log2nx = ilog2(m.nx);
     m.log2ny = ilog2(m.ny);
     m.dx = dx[r];
-    m.d_n = g->d_counters + r;
+    m.d_st = g->d_state + r;
     const size_t bytes = (size_t)m.nx * m.ny * R;
     void** bufs[9] = {&m.phi, &m.psi, &m.omega, &m.xs[0], &m.xs[1], &m.xs[2], &m.xs[3], &m.phi_star,
                       &m.omega_star};
@@ -463,6 +463,12 @@ template <class T>
 void enqueue_step(shf_grid* o) {
   for (auto& cl : o->classes)
     for (int k = 0; k < kKinds; ++k) launch_kind<T>(o, cl, k);
+}
+
+// every member's StepState from its counter; needed once before a run of
+// steps (each step's last kernel then prepares the next step's state)
+void enqueue_state_init(shf_grid* o) {
+  for (auto& cl : o->classes) launch_step_state_init(cl.d_desc, (int)cl.members.size(), o->stream);
 }
 
 void enqueue_steps(shf_grid* o, long long k) {
@@ -840,8 +846,9 @@ int shf_set_step(shf_grid* g, int64_t n) {
   if (!g || n < 0) return SHF_EINVAL;
   if (g->kind == 2) return fail(g, SHF_EINVAL, "the step counter belongs to the ensemble");
   SHF_CUDA(g, cudaSetDevice(g->device));
-  std::vector<long long> v(g->members.size(), (long long)n);
-  SHF_CUDA(g, cudaMemcpyAsync(g->d_counters, v.data(), v.size() * sizeof(long long), cudaMemcpyHostToDevice,
+  // the strain fields are recomputed on the device before the next step
+  std::vector<StepState> v(g->members.size(), StepState{(long long)n, 0, 0.0, 0.0});
+  SHF_CUDA(g, cudaMemcpyAsync(g->d_state, v.data(), v.size() * sizeof(StepState), cudaMemcpyHostToDevice,
                               g->stream));
   SHF_CUDA(g, cudaStreamSynchronize(g->stream));
   g->n = n;
@@ -854,6 +861,7 @@ int shf_step(shf_grid* g, int64_t nsteps) {
   for (auto& m : g->members)
     if (!m.params_set) return fail(g, SHF_ESTATE, "shf_set_params must be called before shf_step");
   SHF_CUDA(g, cudaSetDevice(g->device));
+  if (nsteps > 0) enqueue_state_init(g);
   long long left = nsteps;
   if (left >= kGraphSteps) {
     if (!g->graph) {
@@ -893,6 +901,7 @@ int shf_profile_step(shf_grid* g, int64_t nsteps, double* kernel_ms, int nkinds)
   for (size_t e = 0; e < nev && rc == SHF_OK; ++e)
     if (cudaEventCreate(&ev[e]) != cudaSuccess) rc = fail(g, SHF_ECUDA, "event creation failed");
   if (rc == SHF_OK) {
+    enqueue_state_init(g);
     for (int64_t st = 0; st < nsteps; ++st) {
       for (size_t c = 0; c < ncls; ++c) {
         cudaEvent_t* e = &ev[((size_t)st * ncls + c) * (kKinds + 1)];

@@ -13,6 +13,16 @@ namespace shf {
 // the modes m = 0 .. nx/2-1 of the row's real DFT in a tiled order (see
 // step_kernels.cu); the Nyquist column m = nx/2 is zeroed by the scheme and
 // only the row coefficient of phi* / omega* is kept, to subtract it.
+// Per-member step state in device memory: the step counter n and the strain
+// bookkeeping of the step that starts at n (Section V), evaluated once per
+// step by a single thread (the last kernel of the previous step, or
+// k_step_state_init) so that no kernel evaluates the FP64 strain per thread.
+struct StepState {
+  long long n;
+  long long dK;     // K(n+1) - K(n): nonzero when the strain wraps during the step
+  double s0, s1;    // s(t^n), s(t^{n+1})
+};
+
 struct MemberDesc {
   void* phi;
   void* psi;
@@ -26,7 +36,7 @@ struct MemberDesc {
   void* nyq_phi;     // per row: the real Nyquist coefficient of phi*'s row DFT
   void* nyq_omega;   // per row: the same for omega*
   void* gbuf;        // g = -F/rho (or -F/eta), real; shares phi*'s storage (phi* is dead by then)
-  long long* n;   // device step counter
+  StepState* st;  // device step counter and strain of the current step
   // parameters and derived constants (double; cast to the working precision)
   double a, b, kappa, M, eta, rho, gdot, dt, dx;
   double c_dt_aM;        // dt a M
@@ -125,6 +135,8 @@ template <class T> void launch_sf_cols(const cplx<T>* xs, int log2nx, int log2ny
                                        double* bin_partials, cudaStream_t st);
 void launch_reduce_rows(const double* in, int rows, int cols, double* out, cudaStream_t st);
 template <class T> void set_step_smem_limits();
+// recompute every member's StepState from its counter (before a run of steps)
+void launch_step_state_init(const MemberDesc* d, int nmem, cudaStream_t st);
 template <class T> void set_diag_smem_limits();
 
 }  // namespace shf

@@ -74,18 +74,33 @@ struct Shear {
   T s, w0, w1;
   int d;
   long long dK;   // K(n+1) - K(n): nonzero when the strain wraps during the step
-  __device__ __forceinline__ Shear(const MemberDesc& D, long long n) {
-    double sd, s1;
-    long long K0, K1;
-    strain_dev(n, D.gdot, D.dt, D.ratio, sd, K0);
-    strain_dev(n + 1, D.gdot, D.dt, D.ratio, s1, K1);
-    s = (T)sd;
+  // next = false: s = s(t^n) (stage 1); next = true: s = s(t^{n+1}) (stages 2-3)
+  __device__ __forceinline__ Shear(const StepState& S, bool next) {
+    s = (T)(next ? S.s1 : S.s0);
     w1 = (s < T(0) ? -s : s) * T(0.5);
     w0 = T(1) - w1;
     d = s >= T(0) ? -2 : 2;
-    dK = K1 - K0;
+    dK = S.dK;
   }
 };
+
+// one thread: the StepState of member D for the step starting at n
+__device__ __forceinline__ void step_state_set(const MemberDesc& D, long long n) {
+  double s0, s1;
+  long long K0, K1;
+  strain_dev(n, D.gdot, D.dt, D.ratio, s0, K0);
+  strain_dev(n + 1, D.gdot, D.dt, D.ratio, s1, K1);
+  StepState* S = D.st;
+  S->n = n;
+  S->dK = K1 - K0;
+  S->s0 = s0;
+  S->s1 = s1;
+}
+
+__global__ void k_step_state_init(const MemberDesc* __restrict__ descs, int nmem) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nmem) step_state_set(descs[r], descs[r].st->n);
+}
 
 // ---- asynchronous global -> shared copies (cp.async; the wait is a hardware
 // instruction, not a spin loop)
@@ -187,7 +202,7 @@ __global__ void __launch_bounds__(256) k_stencil1(const MemberDesc* __restrict__
   const int nx = 1 << log2nx, ny = 1 << log2ny, mx = nx - 1, my = ny - 1;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * kTY;
   const bool stokes = D.stokes != 0;
-  const Shear<T> sc(D, *D.n);
+  const Shear<T> sc(*D.st, false);                      // s^n
   const T dt = (T)D.dt, inv2h = (T)D.inv_2h;
   const T* __restrict__ f0 = static_cast<const T*>(D.phi);
   const T* __restrict__ f1 = static_cast<const T*>(D.psi);
@@ -233,7 +248,7 @@ __global__ void __launch_bounds__(256) k_stencil2(const MemberDesc* __restrict__
   const MemberDesc& D = descs[blockIdx.z];
   const int nx = 1 << log2nx, ny = 1 << log2ny, mx = nx - 1, my = ny - 1;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * kTY;
-  const Shear<T> sc(D, *D.n + 1);                        // s^{n+1}
+  const Shear<T> sc(*D.st, true);                        // s^{n+1}
   const T a = (T)D.a, b = (T)D.b, kappa = (T)D.kappa;
   const T inv2h = (T)D.inv_2h, ih2 = (T)D.inv_h2, i4h2 = (T)D.inv_4h2;
   const T cxx = T(1) + sc.s * sc.s, cxy = T(2) * sc.s;
@@ -409,9 +424,7 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_colpass(const MemberDesc
   const T norm = (T)D.inv_nxny, qyu = (T)D.qy_unit;
   const T caM = (T)D.c_dt_aM, cbM = (T)D.c_dt_bM, ckM = (T)D.c_hdt_kM;
   const T cnu = (T)D.c_hdt_nu, dt = (T)D.dt;
-  double s_d;
-  long long K;
-  strain_dev(*D.n + (mode == 0 ? 0 : 1), D.gdot, D.dt, D.ratio, s_d, K);   // s^n for phi, s^{n+1} for flow
+  const double s_d = mode == 0 ? D.st->s0 : D.st->s1;   // s^n for phi, s^{n+1} for flow
 
   const int iters = persistent_iters(nitems, ipc);
   int m = blockIdx.x * ipc + inst;
@@ -533,15 +546,7 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_rowinv(const MemberDesc*
     cp_async_commit();
   };
 
-  long long dK = 0;
-  if (mode == 0 && D.remap) {
-    double s0, s1;
-    long long K0, K1;
-    const long long n = *D.n;
-    strain_dev(n, D.gdot, D.dt, D.ratio, s0, K0);
-    strain_dev(n + 1, D.gdot, D.dt, D.ratio, s1, K1);
-    dK = K1 - K0;
-  }
+  const long long dK = (mode == 0 && D.remap) ? D.st->dK : 0;
   const T rn = T(1) / T(nx);
   const int iters = persistent_iters(nitems, ipc);
   int w = blockIdx.x * ipc + inst;
@@ -610,10 +615,15 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_rowinv(const MemberDesc*
     }
   }
   cp_async_wait_all();
-  if (mode == 1 && blockIdx.x == 0 && threadIdx.x == 0) *D.n += 1;
+  // the next step's state; no CTA of this launch reads it
+  if (mode == 1 && blockIdx.x == 0 && threadIdx.x == 0) step_state_set(D, D.st->n + 1);
 }
 
 // ----------------------------------------------------------------- launchers
+void launch_step_state_init(const MemberDesc* d, int nmem, cudaStream_t st) {
+  k_step_state_init<<<(nmem + 127) / 128, 128, 0, st>>>(d, nmem);
+}
+
 template <class T>
 void launch_step_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int log2ny, const cplx<T>* tw,
                         const LaunchCfg& c, cudaStream_t st) {

@@ -2,8 +2,11 @@
 
 Tolerances (relative L2 per field): FP64 <= 1e-10 and FP32 <= 2e-5 after 200
 steps from the same seeded state; single steps from rough random states
-FP64 <= 1e-11, FP32 <= 1e-5 (psi compared through the operator it solves).  Index work (the wrap remap, checkpoint resume,
-graph replay, ensemble batching, the phi -> -phi symmetry) is bit-exact.
+FP64 <= 1e-11, FP32 <= 1e-5.  FP32 psi is held to an error model of FP32
+arithmetic instead (fp32_model.psi32_model_ratio): the inverse operator of its
+solve amplifies the FP32 rounding of the lowest modes of its right-hand side.
+Index work (the wrap remap, checkpoint resume, graph replay, ensemble batching,
+the phi -> -phi symmetry) is bit-exact.
 """
 import math
 import os
@@ -14,6 +17,7 @@ import pytest
 import oracle
 import paper_0710_5912_gb300 as shf
 from paper_0710_5912_gb300 import inputs
+from fp32_model import PSI32_MODEL_MAX, psi32_model_ratio
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -59,26 +63,20 @@ def rough_state(nx, ny, seed, inertial=True):
     return phi, psi, om
 
 
-def assert_close(got, want, tol, rho, what="", psi_through=None):
-    """Relative L2 per field.  psi_through = (s, dx) compares psi through the
-    operator that produced it (k^4 psi_hat for Stokes, k^2 psi_hat = omega_hat
-    for the inertial solve, k from the sheared wavevector at s): the inverse
-    operators amplify the rounding of the low-k body force by 1/k^4, so from
-    white-noise states psi itself is only as accurate as that conditioning
-    allows, while its image under the operator is not."""
+def assert_close(got, want, tol, rho, what="", prec=FP64, s=0.0, dx=1.0):
+    """Relative L2 per field, except FP32 psi, which is held to the FP32 error
+    model of fp32_model.psi32_model_ratio (its plain relative L2 is limited by
+    the conditioning of the solve)."""
     names = ("phi", "psi", "omega")
     for name, a, b in zip(names, got, want):
         if rho == 0 and name == "omega":
             assert np.abs(a).max() == 0.0
             continue
-        if name == "psi" and psi_through is not None:
-            s, dx = psi_through
-            ny, nx = a.shape
-            QX, QY, _ = oracle.wavenumbers(nx, ny, dx)
-            k2 = oracle.sheared_k2(QX, QY, s)
-            w = k2 * k2 if rho == 0 else k2
-            a = np.real(np.fft.ifft2(w * np.fft.fft2(a)))
-            b = np.real(np.fft.ifft2(w * np.fft.fft2(b)))
+        if name == "psi" and prec == FP32:
+            q = psi32_model_ratio(a, b, s, dx, rho)
+            assert q <= PSI32_MODEL_MAX, f"{what} psi: error/model {q:.2f} > {PSI32_MODEL_MAX} " \
+                                         f"(rel L2 {rel_l2(a, b):.2e})"
+            continue
         err = rel_l2(a, b)
         assert err <= tol, f"{what} {name}: rel L2 {err:.3e} > {tol:g}"
 
@@ -101,7 +99,7 @@ def test_one_step_from_rough_state(prec, rho, shape, strain):
     got = gpu_run(nx, ny, prec, p, fields, n0, 2)
     want = oracle_run(p, fields, n0, 2)
     s_end = oracle.strain(n0 + 2, p.gdot, p.dt, nx, ny)[0]
-    assert_close(got, want, TOL_1[prec], rho, f"{shape} {strain}", psi_through=(s_end, p.dx))
+    assert_close(got, want, TOL_1[prec], rho, f"{shape} {strain}", prec, s_end, p.dx)
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
@@ -119,7 +117,7 @@ def test_steps_across_strain_wraps(prec, rho, shape, remap):
     assert K_end >= 2
     got = gpu_run(nx, ny, prec, p, fields, 3, nsteps, remap)
     want = oracle_run(p, fields, 3, nsteps, remap)
-    assert_close(got, want, TOL_200[prec], rho, f"wrap {shape} remap={remap}", psi_through=(s_end, 1.0))
+    assert_close(got, want, TOL_200[prec], rho, f"wrap {shape} remap={remap}", prec, s_end, 1.0)
 
 
 # ------------------------------------------------------------ 200-step runs
@@ -153,7 +151,7 @@ def test_inertial_256_fp32_200_steps(gdot):
     fields = inputs.quench_state(nx, ny, 1)
     got = gpu_run(nx, ny, FP32, p, fields, 0, 200)
     want = oracle_run(p, fields, 0, 200)
-    assert_close(got, want, 2e-5, 1.0, f"256^2 gdot={gdot}")
+    assert_close(got, want, 2e-5, 1.0, f"256^2 gdot={gdot}", FP32, oracle.strain(200, gdot, p.dt, nx, ny)[0])
 
 
 @pytest.mark.parametrize("rho", [0.0, 1.0])
@@ -174,7 +172,7 @@ def test_config_1024_side_by_side(rho):
     fields = inputs.quench_state(nx, ny, 3)
     got = gpu_run(nx, ny, FP32, p, fields, 0, 3)
     want = oracle_run(p, fields, 0, 3)
-    assert_close(got, want, 1e-5, rho, f"1024^2 rho={rho}")
+    assert_close(got, want, 1e-5, rho, f"1024^2 rho={rho}", FP32, oracle.strain(3, p.gdot, p.dt, nx, ny)[0])
 
 
 def test_config_4096_inertial_full_size_step():
@@ -188,7 +186,7 @@ def test_config_4096_inertial_full_size_step():
     fields = (phi, psi, om)
     got = gpu_run(nx, ny, FP32, p, fields, 1234, 1)
     want = oracle_run(p, fields, 1234, 1)
-    assert_close(got, want, 1e-5, 1.0, "4096^2")
+    assert_close(got, want, 1e-5, 1.0, "4096^2", FP32, oracle.strain(1235, p.gdot, p.dt, nx, ny)[0])
 
 
 # --------------------------------------------------------------- invariants
@@ -325,7 +323,8 @@ def test_ensemble_members_match_single_runs(prec):
         for x, y in zip(got, single):
             assert np.array_equal(x, y), f"member {r}"
         want = oracle_run(p, fields, 0, 120)
-        assert_close(got, want, TOL_200[prec], rho, f"member {r}")
+        assert_close(got, want, TOL_200[prec], rho, f"member {r}", prec,
+                     oracle.strain(120, gdot, dt, nxs[r], nys[r])[0])
         assert ens.members[r].get_time()[0] == 120
     ens.close()
 
