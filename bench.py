@@ -180,13 +180,23 @@ class ClockSampler:
 
 
 def allreduce_max(x, world):
+    """Max of a per-rank scalar over all ranks (NCCL on GPUs, gloo on CPUs)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(elapsed_ms_local, steps, world, points_per_rank=NX * NY):
+    """(slowest rank's elapsed ms, grid-point updates/s of all ranks together):
+    every rank advances its own replica, so the job's work is world replicas'
+    points x steps and its time is the slowest rank's."""
+    elapsed = allreduce_max(elapsed_ms_local, world)
+    return elapsed, world * points_per_rank * steps / (elapsed / 1e3)
 
 
 def barrier(world):
@@ -201,6 +211,8 @@ def cpu_oracle_step_rate(n, steps=1):
     from paper_0710_5912_gb300 import inputs
     p = oracle.Params(**PARAMS)
     fields = inputs.quench_state(n, n, SEED, AMP)
+    if steps <= 0:
+        return 0.0, 0.0
     t0 = time.perf_counter()
     fields = oracle.run(*fields, steps, p)
     dt = time.perf_counter() - t0
@@ -211,9 +223,11 @@ def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
         return 0
-    n_sample = 1024
-    for _ in range(args.warmup):
-        cpu_oracle_step_rate(n_sample, 1)
+    # a bounded sample: each step is one oracle step of the workload's scheme and
+    # parameters on a 256 x 256 grid (about 40 ms), so K = 2000 steps stay near
+    # a minute and a half; the rate is per grid point, like the GPU arm's
+    n_sample = 256
+    cpu_oracle_step_rate(n_sample, args.warmup)
     rate, secs = cpu_oracle_step_rate(n_sample, args.steps)
     sample = (f"each step: one oracle step (float64 numpy, 1 thread) of the workload's scheme and "
               f"parameters on a {n_sample}x{n_sample} grid; {args.steps} steps in {secs:.1f} s")
@@ -267,9 +281,8 @@ def main():
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
-    elapsed_ms = allreduce_max(e0.elapsed_time(e1), world)
+    elapsed_ms, value = whole_job_rate(e0.elapsed_time(e1), args.steps, world)
     ms_per_step = elapsed_ms / args.steps
-    value = world * NX * NY * args.steps / (elapsed_ms / 1e3)
     g.sync()
 
     # graph-replay path (shf_step) over the same number of steps, for reference
@@ -362,7 +375,8 @@ def main():
                            "parallelism": f"replicas x{world}" if world > 1 else "single grid",
                            "l2": "state + scratch 448 MiB > L2: inputs larger than L2, no flush"},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e,
-                "gpu_launches": len(KERNEL_REALS_PER_POINT) * args.steps,
+                # eight step kernels per step plus the one state-seeding launch of the run
+                "gpu_launches": len(KERNEL_REALS_PER_POINT) * args.steps + 1,
                 "graph_ms_per_step": graph_ms_per_step,
                 "step_algorithmic_bytes": step_bytes,
                 "step_hbm_frac": step_bytes / (ms_per_step * 1e-3) / 1e9 / peak,
