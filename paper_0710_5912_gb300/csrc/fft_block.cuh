@@ -272,6 +272,85 @@ __device__ __forceinline__ void fft_reg(C (&v)[kP], int log2N, int t, C* buf, co
   }
 }
 
+// Two transforms of the same length in lock step (FP32): a[] and b[] share
+// every twiddle factor, and each exchange moves both as one 16-byte vector
+// per position (buf: padded_len(N) float4).  Same register layout and stage
+// schedule as fft_reg.
+template <bool INV, int LR, bool LAST>
+__device__ __forceinline__ void fft_reg2_stage(float2 (&a)[kP], float2 (&b)[kP], int log2N, int log2Ns, int t,
+                                               float4* buf, const float2* __restrict__ twt) {
+  using C = float2;
+  constexpr int R = 1 << LR;
+  constexpr int B = kP >> LR;
+  const int T = 1 << (log2N - kLogP);
+  const int Ns = 1 << log2Ns;
+  C wa[R], wb[R];
+#pragma unroll
+  for (int bb = 0; bb < B; ++bb) {
+    const int j = t + bb * T;
+    const int k = j & (Ns - 1);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      wa[r] = a[bb + r * B];
+      wb[r] = b[bb + r * B];
+    }
+    if (log2Ns > 0) {
+      const float4* r4 = reinterpret_cast<const float4*>(twt + stage_table_offset(log2Ns, LR) + k * R);
+      C f[R];
+#pragma unroll
+      for (int h = 0; h < R / 2; ++h) {
+        const float4 x = __ldg(r4 + h);
+        f[2 * h] = C{x.x, x.y};
+        f[2 * h + 1] = C{x.z, x.w};
+      }
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        const C fr = INV ? f[r] : cconj(f[r]);
+        wa[r] = cmul(wa[r], fr);
+        wb[r] = cmul(wb[r], fr);
+      }
+    }
+    dft_radix<INV, LR>(wa);
+    dft_radix<INV, LR>(wb);
+    if (LAST) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        a[bb + r * B] = wa[r];
+        b[bb + r * B] = wb[r];
+      }
+    } else {
+      const int base = ((j - k) << LR) + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[pad16(base + r * Ns)] = make_float4(wa[r].x, wa[r].y, wb[r].x, wb[r].y);
+    }
+  }
+  if (!LAST) {
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kP; ++q) {
+      const float4 x = buf[pad16(t + q * T)];
+      a[q] = C{x.x, x.y};
+      b[q] = C{x.z, x.w};
+    }
+    __syncthreads();
+  }
+}
+
+template <bool INV>
+__device__ __forceinline__ void fft_reg2(float2 (&a)[kP], float2 (&b)[kP], int log2N, int t, float4* buf,
+                                         const float2* __restrict__ tw) {
+  int log2Ns = 0;
+  while (log2N - log2Ns > kLogP) {
+    fft_reg2_stage<INV, kLogP, false>(a, b, log2N, log2Ns, t, buf, tw);
+    log2Ns += kLogP;
+  }
+  switch (log2N - log2Ns) {
+    case 3: fft_reg2_stage<INV, 3, true>(a, b, log2N, log2Ns, t, buf, tw); break;
+    case 2: fft_reg2_stage<INV, 2, true>(a, b, log2N, log2Ns, t, buf, tw); break;
+    default: fft_reg2_stage<INV, 1, true>(a, b, log2N, log2Ns, t, buf, tw); break;
+  }
+}
+
 // v[q] = X[t + T q] -> buf (padded, natural order), followed by a barrier.
 template <class C>
 __device__ __forceinline__ void reg_to_smem(const C (&v)[kP], int log2N, int t, C* buf) {

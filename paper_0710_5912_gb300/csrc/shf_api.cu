@@ -199,10 +199,12 @@ void configure_class_t(SizeClass& cl) {
   cl.cfg[KIND_ROWFWD_PHI] =
       persistent_cfg<T>(KIND_ROWFWD_PHI, nx, ny / 2, 3 * (ny / 2), rowfwd_inst_bytes(nx, R), nmem);
   cl.cfg[KIND_ROWFWD_G] = persistent_cfg<T>(KIND_ROWFWD_G, nx, ny / 2, ny / 2, rowfwd_inst_bytes(nx, R), nmem);
+  // column items: whole 16-byte chunks (two modes in FP32, one in FP64)
+  const int ncol_items = R == 4 ? nx / 4 : nx / 2;
   cl.cfg[KIND_COLPASS_PHI] =
-      persistent_cfg<T>(KIND_COLPASS_PHI, ny, nx / 2, nx / 2, colpass_inst_bytes(ny, R), nmem);
+      persistent_cfg<T>(KIND_COLPASS_PHI, ny, ncol_items, ncol_items, colpass_inst_bytes(ny, R), nmem);
   cl.cfg[KIND_COLPASS_FLOW] =
-      persistent_cfg<T>(KIND_COLPASS_FLOW, ny, nx / 2, nx / 2, colpass_inst_bytes(ny, R), nmem);
+      persistent_cfg<T>(KIND_COLPASS_FLOW, ny, ncol_items, ncol_items, colpass_inst_bytes(ny, R), nmem);
   cl.cfg[KIND_ROWINV_PHI] = persistent_cfg<T>(KIND_ROWINV_PHI, nx, ny / 2, ny / 2, rowinv_inst_bytes(nx, R), nmem);
   cl.cfg[KIND_ROWINV_FLOW] = persistent_cfg<T>(KIND_ROWINV_FLOW, nx, ny / 2, ny, rowinv_inst_bytes(nx, R), nmem);
   cl.sfrows = sf_row_cfg(nx, ny, nx * Cx);

@@ -68,14 +68,17 @@ __device__ __forceinline__ void strain_dev(long long n, double gdot, double dt, 
 // Shared memory of one instance of the persistent transform kernels (rounded
 // to 128 bytes so that every instance's staging buffer is 16-byte aligned):
 // rowfwd stages two real rows and holds the padded FFT buffer; colpass stages
-// two complex columns plus the buffer; rowinv stages the 32-byte chunks of a
-// row pair (nx complex) plus the buffer.
+// one x-spectral chunk column of each input field plus the buffer; rowinv
+// stages the 32-byte chunks of a row pair (nx complex) plus the buffer.
 __host__ __device__ constexpr size_t round128(size_t b) { return (b + 127) & ~(size_t)127; }
 __host__ __device__ constexpr size_t rowfwd_inst_bytes(int nx, size_t real_bytes) {
   return round128(2 * (size_t)nx * real_bytes + (size_t)padded_len(nx) * 2 * real_bytes);
 }
-__host__ __device__ constexpr size_t colpass_inst_bytes(int ny, size_t real_bytes) {
-  return round128((2 * (size_t)ny + (size_t)padded_len(ny)) * 2 * real_bytes);
+// colpass stages two 16-byte-per-row columns (one x-spectral chunk of each
+// input field: 2 complex floats or 1 complex double per row) plus a 16-byte
+// exchange buffer, in both precisions
+__host__ __device__ constexpr size_t colpass_inst_bytes(int ny, size_t /*real_bytes*/) {
+  return round128((2 * (size_t)ny + (size_t)padded_len(ny)) * 16);
 }
 __host__ __device__ constexpr size_t rowinv_inst_bytes(int nx, size_t real_bytes) {
   return round128(((size_t)nx + (size_t)padded_len(nx)) * 2 * real_bytes);

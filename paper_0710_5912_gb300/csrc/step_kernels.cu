@@ -132,8 +132,9 @@ __device__ __forceinline__ void split_pair(const C* z, int m, int mx, C& A, C& B
   B = C{(zk.y - zc.y) * T(0.5), -(zk.x - zc.x) * T(0.5)};
 }
 
-// Z holds FFT(row j0 + i row j0+1) of one field: both half spectra -> dst,
-// whole 2 CL-element chunks per thread.
+// Z holds FFT(row j0 + i row j0+1) of one field: both half spectra -> dst.
+// A thread writes whole chunks of the pair: 2 CL elements = 32 contiguous
+// bytes (a full sector), as two 16-byte stores in FP32.
 template <int LC, class C>
 __device__ __forceinline__ void write_pair_rows(const C* z, C* dst, int j0, int nx, int ny, int t, int Tthreads) {
   constexpr int CL = 1 << LC;
@@ -141,32 +142,18 @@ __device__ __forceinline__ void write_pair_rows(const C* z, C* dst, int j0, int 
   const int nchunk = (nx >> 1) >> LC;
   for (int cb = t; cb < nchunk; cb += Tthreads) {
     C* p = dst + ((((size_t)cb * ny) + j0) << LC);
+    C A[CL], B[CL];
 #pragma unroll
-    for (int c = 0; c < CL; ++c) {
-      C A, B;
-      split_pair(z, (cb << LC) + c, mx, A, B);
-      p[c] = A;
-      p[CL + c] = B;
-    }
-  }
-}
-
-// Z holds FFT(a + i b) of row j of two fields: a -> dstA, b -> dstB.
-template <int LC, class C>
-__device__ __forceinline__ void write_one_row(const C* z, C* dstA, C* dstB, int j, int nx, int ny, int t,
-                                              int Tthreads) {
-  constexpr int CL = 1 << LC;
-  const int mx = nx - 1;
-  const int nchunk = (nx >> 1) >> LC;
-  for (int cb = t; cb < nchunk; cb += Tthreads) {
-    C* pa = dstA + ((((size_t)cb * ny) + j) << LC);
-    C* pb = dstB + ((((size_t)cb * ny) + j) << LC);
+    for (int c = 0; c < CL; ++c) split_pair(z, (cb << LC) + c, mx, A[c], B[c]);
+    if constexpr (CL == 2) {
+      reinterpret_cast<float4*>(p)[0] = make_float4(A[0].x, A[0].y, A[1].x, A[1].y);
+      reinterpret_cast<float4*>(p)[1] = make_float4(B[0].x, B[0].y, B[1].x, B[1].y);
+    } else {
 #pragma unroll
-    for (int c = 0; c < CL; ++c) {
-      C A, B;
-      split_pair(z, (cb << LC) + c, mx, A, B);
-      pa[c] = A;
-      pb[c] = B;
+      for (int c = 0; c < CL; ++c) {
+        p[c] = A[c];
+        p[CL + c] = B[c];
+      }
     }
   }
 }
@@ -286,11 +273,11 @@ __global__ void __launch_bounds__(256) k_stencil2(const MemberDesc* __restrict__
 }
 
 // ====================================================== forward row transforms
-// Work items: mode 0 (phi): per row pair p, item 0 = (phi*, f) of row 2p,
-// item 1 = the same of row 2p+1, item 2 = omega* of rows (2p, 2p+1) for
-// inertial members; mode 1 (g): one item per row pair.  Each item stages two
-// real rows (a, b) in shared memory; the transform is of a + i b (for f the
-// cube of the staged phi row is taken on the fly).
+// Work items: mode 0 (phi): per row pair p = rows (2p, 2p+1), item 0 = phi*,
+// item 1 = f = phi^3, item 2 = omega* (inertial members); mode 1 (g): one item
+// per row pair.  Each item stages the two real rows (a, b) in shared memory and
+// transforms a + i b (for f the staged phi rows are cubed on the fly), so every
+// output chunk of the pair is one whole 32-byte piece.
 template <class T>
 __global__ void __launch_bounds__(512, min_ctas<T>()) k_rowfwd(const MemberDesc* __restrict__ descs, int log2nx, int log2ny,
                                                 const cplx<T>* __restrict__ tw, int mode) {
@@ -321,8 +308,9 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_rowfwd(const MemberDesc*
         ra = gb + ((size_t)(2 * p) << log2nx);
         rb = gb + ((size_t)(2 * p + 1) << log2nx);
       } else if (sub < 2) {
-        ra = phis + ((size_t)(2 * p + sub) << log2nx);
-        rb = phi + ((size_t)(2 * p + sub) << log2nx);
+        const T* src = sub == 0 ? phis : phi;             // phi* pair, or phi pair (cubed on the fly)
+        ra = src + ((size_t)(2 * p) << log2nx);
+        rb = src + ((size_t)(2 * p + 1) << log2nx);
       } else {
         ra = oms + ((size_t)(2 * p) << log2nx);
         rb = oms + ((size_t)(2 * p + 1) << log2nx);
@@ -339,7 +327,7 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_rowfwd(const MemberDesc*
   for (int it = 0; it < iters; ++it, w += stride) {
     const bool active = w < nitems;
     const int p = w / nsub, sub = w - p * nsub;
-    const bool cube = mode == 0 && sub < 2;
+    const bool cube = mode == 0 && sub == 1;
     cp_async_wait_all();
     __syncthreads();
     C v[kP];
@@ -347,7 +335,7 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_rowfwd(const MemberDesc*
     for (int q = 0; q < kP; ++q) {
       const int i = t + q * Tf;
       const T a = stage[i], bb = stage[nx + i];
-      v[q] = C{a, cube ? (bb * bb) * bb : bb};
+      v[q] = cube ? C{(a * a) * a, (bb * bb) * bb} : C{a, bb};
     }
     __syncthreads();                                    // stage free
     issue(w + stride);                                  // next item streams in during the transform
@@ -357,8 +345,12 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_rowfwd(const MemberDesc*
       if (mode == 1) {
         write_pair_rows<LC>(Z, static_cast<C*>(D.xs_g), 2 * p, nx, ny, t, Tf);
       } else if (sub < 2) {
-        write_one_row<LC>(Z, static_cast<C*>(D.xs_phi), static_cast<C*>(D.xs_f), 2 * p + sub, nx, ny, t, Tf);
-        if (t == 0) static_cast<T*>(D.nyq_phi)[2 * p + sub] = Z[pad16(nx >> 1)].x;   // phi*'s row Nyquist
+        write_pair_rows<LC>(Z, static_cast<C*>(sub == 0 ? D.xs_phi : D.xs_f), 2 * p, nx, ny, t, Tf);
+        if (sub == 0 && t == 0) {                        // phi*'s row Nyquist coefficients
+          const C zn = Z[pad16(nx >> 1)];
+          static_cast<T*>(D.nyq_phi)[2 * p] = zn.x;
+          static_cast<T*>(D.nyq_phi)[2 * p + 1] = zn.y;
+        }
       } else {
         write_pair_rows<LC>(Z, static_cast<C*>(D.xs_w), 2 * p, nx, ny, t, Tf);
         if (t == 0) {
@@ -388,6 +380,68 @@ __device__ __forceinline__ void stage_column(cplx<T>* st, const cplx<T>* __restr
     copy_async(st, src + (size_t)m * ny, ny * (int)sizeof(C), t, Tc);
   } else {
     for (int n = t; n < ny; n += Tc) cp_async8(st + n, src + xs_idx(n, m, ny, LC));
+  }
+}
+
+// Constants of the column-pass multipliers (Appendix B item 1 for mode 0;
+// Eq. forOmega with the Poisson solve, or the Stokes solve, for mode 1).
+template <class T>
+struct ColConsts {
+  T norm, qyu, caM, cbM, ckM, cnu, dt;
+  double qx_unit, s_d;
+  int ny;
+  bool stokes;
+  __device__ __forceinline__ ColConsts(const MemberDesc& D, int mode, int ny_)
+      : norm((T)D.inv_nxny), qyu((T)D.qy_unit), caM((T)D.c_dt_aM), cbM((T)D.c_dt_bM), ckM((T)D.c_hdt_kM),
+        cnu((T)D.c_hdt_nu), dt((T)D.dt), qx_unit(D.qx_unit),
+        s_d(mode == 0 ? D.st->s0 : D.st->s1),        // s^n for phi, s^{n+1} for flow
+        ny(ny_), stokes(D.stokes != 0) {}
+};
+
+// The multiplier at mode (m, row nn) of the column transform, in place:
+// mode 0: va = phi*_hat -> increment of phi_hat (x norm), vb = f_hat;
+// mode 1: va = g_hat -> psi_hat (x norm), vb = omega*_hat -> increment (x norm).
+// qx = m q_unit and sqx = s q_x, both formed in double.
+template <class T>
+__device__ __forceinline__ void col_multiply(int mode, const ColConsts<T>& K, int m, T qx, T sqx, int nn,
+                                             cplx<T>& va, cplx<T>& vb) {
+  using C = cplx<T>;
+  const int ns = nn < (K.ny >> 1) ? nn : nn - K.ny;
+  const T ky = (T)ns * K.qyu - sqx;
+  const T k2 = qx * qx + ky * ky;
+  const bool nyq_row = nn == (K.ny >> 1);
+  const T norm = K.norm;
+  if (mode == 0) {
+    const C P = va, F = vb;
+    if (nyq_row) {
+      va = C{-P.x * norm, -P.y * norm};                 // Nyquist row of phi^{n+1} -> 0
+    } else {
+      const T c4 = K.ckM * (k2 * k2);
+      const T aa = K.caM * k2 - T(2) * c4;
+      const T bbm = K.cbM * k2;
+      const T inv = norm / (T(1) + c4);
+      va = C{(aa * P.x - bbm * F.x) * inv, (aa * P.y - bbm * F.y) * inv};
+    }
+  } else {
+    const bool zero = nyq_row || (m == 0 && nn == 0);
+    const C G = va;
+    if (K.stokes) {
+      const T inv = zero ? T(0) : norm / (k2 * k2);
+      va = C{G.x * inv, G.y * inv};
+    } else {
+      const C Wv = vb;
+      if (zero) {
+        va = C{T(0), T(0)};
+        vb = C{-Wv.x * norm, -Wv.y * norm};             // omega^{n+1} -> 0 there
+      } else {
+        const T cc = K.cnu * k2;
+        const T inv = T(1) / (T(1) + cc);
+        const C dw = C{(-T(2) * cc * Wv.x + K.dt * G.x) * inv, (-T(2) * cc * Wv.y + K.dt * G.y) * inv};
+        const T ik = norm / k2;
+        va = C{(Wv.x + dw.x) * ik, (Wv.y + dw.y) * ik};
+        vb = C{dw.x * norm, dw.y * norm};
+      }
+    }
   }
 }
 
@@ -421,10 +475,7 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_colpass(const MemberDesc
     cp_async_commit();
   };
 
-  const T norm = (T)D.inv_nxny, qyu = (T)D.qy_unit;
-  const T caM = (T)D.c_dt_aM, cbM = (T)D.c_dt_bM, ckM = (T)D.c_hdt_kM;
-  const T cnu = (T)D.c_hdt_nu, dt = (T)D.dt;
-  const double s_d = mode == 0 ? D.st->s0 : D.st->s1;   // s^n for phi, s^{n+1} for flow
+  const ColConsts<T> K(D, mode, ny);
 
   const int iters = persistent_iters(nitems, ipc);
   int m = blockIdx.x * ipc + inst;
@@ -445,49 +496,11 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_colpass(const MemberDesc
     issue(m + stride);
     fft_reg<false>(va, log2ny, t, buf, tw);
     if (two) fft_reg<false>(vb, log2ny, t, buf, tw);
-    const double qx_d = mm * D.qx_unit;
+    const double qx_d = mm * K.qx_unit;
     const T qx = (T)qx_d;
-    const T sqx = (T)(s_d * qx_d);                      // s q_x formed in double
+    const T sqx = (T)(K.s_d * qx_d);                    // s q_x formed in double
 #pragma unroll
-    for (int q = 0; q < kP; ++q) {
-      const int nn = t + q * Tc;
-      const int ns = nn < (ny >> 1) ? nn : nn - ny;
-      const T ky = (T)ns * qyu - sqx;
-      const T k2 = qx * qx + ky * ky;
-      const bool nyq_row = nn == (ny >> 1);
-      if (mode == 0) {
-        const C P = va[q], F = vb[q];
-        if (nyq_row) {
-          va[q] = C{-P.x * norm, -P.y * norm};          // Nyquist row of phi^{n+1} -> 0
-        } else {
-          const T c4 = ckM * (k2 * k2);
-          const T aa = caM * k2 - T(2) * c4;
-          const T bbm = cbM * k2;
-          const T inv = norm / (T(1) + c4);
-          va[q] = C{(aa * P.x - bbm * F.x) * inv, (aa * P.y - bbm * F.y) * inv};
-        }
-      } else {
-        const bool zero = nyq_row || (mm == 0 && nn == 0);
-        const C G = va[q];
-        if (stokes) {
-          const T inv = zero ? T(0) : norm / (k2 * k2);
-          va[q] = C{G.x * inv, G.y * inv};
-        } else {
-          const C Wv = vb[q];
-          if (zero) {
-            va[q] = C{T(0), T(0)};
-            vb[q] = C{-Wv.x * norm, -Wv.y * norm};      // omega^{n+1} -> 0 there
-          } else {
-            const T cc = cnu * k2;
-            const T inv = T(1) / (T(1) + cc);
-            const C dw = C{(-T(2) * cc * Wv.x + dt * G.x) * inv, (-T(2) * cc * Wv.y + dt * G.y) * inv};
-            const T ik = norm / k2;
-            va[q] = C{(Wv.x + dw.x) * ik, (Wv.y + dw.y) * ik};
-            vb[q] = C{dw.x * norm, dw.y * norm};
-          }
-        }
-      }
-    }
+    for (int q = 0; q < kP; ++q) col_multiply<T>(mode, K, mm, qx, sqx, t + q * Tc, va[q], vb[q]);
     fft_reg<true>(va, log2ny, t, buf, tw);
     if (active) {
 #pragma unroll
@@ -498,6 +511,94 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_colpass(const MemberDesc
       if (active) {
 #pragma unroll
         for (int q = 0; q < kP; ++q) in1[xs_idx(t + q * Tc, m, ny, LC)] = vb[q];
+      }
+    }
+  }
+  cp_async_wait_all();
+}
+
+// FP32 column pass over whole chunks: item cb = the two modes m = 2cb, 2cb+1,
+// whose ny rows are one contiguous 16-byte-per-row run in the x-spectral
+// layout.  Both columns are staged with 16-byte copies, transformed in lock
+// step (shared twiddles, 16-byte exchanges) and written back as whole 16-byte
+// rows, so no sector is touched twice.
+__global__ void __launch_bounds__(512, 1) k_colpass_pair(const MemberDesc* __restrict__ descs, int log2nx,
+                                                        int log2ny, const float2* __restrict__ tw, int mode) {
+  using T = float;
+  using C = float2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const MemberDesc& D = descs[blockIdx.y];
+  const int nx = 1 << log2nx, ny = 1 << log2ny;
+  const int Tc = ny >> kLogP;
+  const int ipc = blockDim.x / Tc;
+  const int inst = threadIdx.x / Tc, t = threadIdx.x - inst * Tc;
+  const int nitems = nx >> 2;
+  const int stride = gridDim.x * ipc;
+  const bool stokes = D.stokes != 0;
+  const bool two = mode == 0 || !stokes;                // second input field
+  unsigned char* base = smem_raw + (size_t)inst * colpass_inst_bytes(ny, sizeof(T));
+  float4* st0 = reinterpret_cast<float4*>(base);
+  float4* st1 = st0 + ny;
+  float4* buf = st1 + ny;
+  float4* in0 = static_cast<float4*>(mode == 0 ? D.xs_phi : D.xs_g);
+  float4* in1 = static_cast<float4*>(mode == 0 ? D.xs_f : D.xs_w);
+
+  auto issue = [&](int cb) {
+    if (cb < nitems) {
+      copy_async(st0, in0 + (size_t)cb * ny, ny * 16, t, Tc);
+      if (two) copy_async(st1, in1 + (size_t)cb * ny, ny * 16, t, Tc);
+    }
+    cp_async_commit();
+  };
+
+  const ColConsts<T> K(D, mode, ny);
+  const int iters = persistent_iters(nitems, ipc);
+  int cb = blockIdx.x * ipc + inst;
+  issue(cb);
+  for (int it = 0; it < iters; ++it, cb += stride) {
+    const bool active = cb < nitems;
+    cp_async_wait_all();
+    __syncthreads();
+    C a0[kP], b0[kP], a1[kP], b1[kP];                   // a: mode 2cb, b: mode 2cb+1; 0/1: the two fields
+#pragma unroll
+    for (int q = 0; q < kP; ++q) {
+      const float4 x = st0[t + q * Tc];
+      a0[q] = C{x.x, x.y};
+      b0[q] = C{x.z, x.w};
+    }
+    if (two) {
+#pragma unroll
+      for (int q = 0; q < kP; ++q) {
+        const float4 x = st1[t + q * Tc];
+        a1[q] = C{x.x, x.y};
+        b1[q] = C{x.z, x.w};
+      }
+    }
+    __syncthreads();                                    // stage free
+    issue(cb + stride);
+    fft_reg2<false>(a0, b0, log2ny, t, buf, tw);
+    if (two) fft_reg2<false>(a1, b1, log2ny, t, buf, tw);
+    const int m0 = active ? 2 * cb : 0, m1 = m0 + 1;
+    const double qa_d = m0 * K.qx_unit, qb_d = m1 * K.qx_unit;
+    const T qa = (T)qa_d, qb = (T)qb_d;
+    const T sqa = (T)(K.s_d * qa_d), sqb = (T)(K.s_d * qb_d);   // s q_x formed in double
+#pragma unroll
+    for (int q = 0; q < kP; ++q) {
+      col_multiply<T>(mode, K, m0, qa, sqa, t + q * Tc, a0[q], a1[q]);
+      col_multiply<T>(mode, K, m1, qb, sqb, t + q * Tc, b0[q], b1[q]);
+    }
+    fft_reg2<true>(a0, b0, log2ny, t, buf, tw);
+    if (active) {
+      float4* o = in0 + (size_t)cb * ny;
+#pragma unroll
+      for (int q = 0; q < kP; ++q) o[t + q * Tc] = make_float4(a0[q].x, a0[q].y, b0[q].x, b0[q].y);
+    }
+    if (mode == 1 && !stokes) {
+      fft_reg2<true>(a1, b1, log2ny, t, buf, tw);
+      if (active) {
+        float4* o = in1 + (size_t)cb * ny;
+#pragma unroll
+        for (int q = 0; q < kP; ++q) o[t + q * Tc] = make_float4(a1[q].x, a1[q].y, b1[q].x, b1[q].y);
       }
     }
   }
@@ -640,7 +741,10 @@ void launch_step_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int
       k_rowfwd<T><<<dim3(c.grid_x, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw, 0);
       break;
     case KIND_COLPASS_PHI:
-      k_colpass<T><<<dim3(c.grid_x, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw, 0);
+      if constexpr (sizeof(T) == 4)
+        k_colpass_pair<<<dim3(c.grid_x, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw, 0);
+      else
+        k_colpass<T><<<dim3(c.grid_x, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw, 0);
       break;
     case KIND_ROWINV_PHI:
       k_rowinv<T><<<dim3(c.grid_x, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw, 0);
@@ -657,7 +761,10 @@ void launch_step_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int
       k_rowfwd<T><<<dim3(c.grid_x, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw, 1);
       break;
     case KIND_COLPASS_FLOW:
-      k_colpass<T><<<dim3(c.grid_x, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw, 1);
+      if constexpr (sizeof(T) == 4)
+        k_colpass_pair<<<dim3(c.grid_x, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw, 1);
+      else
+        k_colpass<T><<<dim3(c.grid_x, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw, 1);
       break;
     default:
       k_rowinv<T><<<dim3(c.grid_x, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw, 1);
@@ -674,7 +781,9 @@ int step_kernel_occupancy(int kind, int threads, size_t smem) {
     case KIND_ROWFWD_PHI:
     case KIND_ROWFWD_G: f = (const void*)k_rowfwd<T>; break;
     case KIND_COLPASS_PHI:
-    case KIND_COLPASS_FLOW: f = (const void*)k_colpass<T>; break;
+    case KIND_COLPASS_FLOW:
+      f = sizeof(T) == 4 ? (const void*)k_colpass_pair : (const void*)k_colpass<T>;
+      break;
     default: f = (const void*)k_rowinv<T>; break;
   }
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads, smem) != cudaSuccess) nb = 1;
@@ -686,6 +795,7 @@ void set_step_smem_limits() {
   const int lim = 220 * 1024;   // dynamic part; leaves room for static shared memory
   cudaFuncSetAttribute(k_rowfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_colpass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  if (sizeof(T) == 4) cudaFuncSetAttribute(k_colpass_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_rowinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
