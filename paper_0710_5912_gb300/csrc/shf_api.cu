@@ -190,11 +190,15 @@ template <class T>
 void configure_class_t(SizeClass& cl) {
   const size_t R = sizeof(T), Cx = 2 * R;
   const int nx = cl.nx, ny = cl.ny, nmem = (int)cl.members.size();
+  // stencil tiles of TX = min(nx, 128) by TY = min(ny, 32), 4 x 4 outputs per thread
+  const int TX = nx < 128 ? nx : 128, TY = ny < 32 ? ny : 32;
   LaunchCfg st{};
-  st.grid_x = nx / (nx < 128 ? nx : 128);
-  st.grid_y = ny / 8;
-  st.threads = 256;
+  st.grid_x = nx / TX;
+  st.grid_y = ny / TY;
+  st.threads = (TX / 4) * (TY / 4);
+  st.smem = stencil1_smem_bytes(TX, TY, R);
   cl.cfg[KIND_STENCIL1] = st;
+  st.smem = stencil2_smem_bytes(TX, TY, R);
   cl.cfg[KIND_STENCIL2] = st;
   cl.cfg[KIND_ROWFWD_PHI] =
       persistent_cfg<T>(KIND_ROWFWD_PHI, nx, ny / 2, 3 * (ny / 2), rowfwd_inst_bytes(nx, R), nmem);

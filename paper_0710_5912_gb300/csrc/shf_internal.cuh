@@ -71,6 +71,15 @@ __device__ __forceinline__ void strain_dev(long long n, double gdot, double dt, 
 // one x-spectral chunk column of each input field plus the buffer; rowinv
 // stages the 32-byte chunks of a row pair (nx complex) plus the buffer.
 __host__ __device__ constexpr size_t round128(size_t b) { return (b + 127) & ~(size_t)127; }
+// Stencil tiles (dynamic shared memory): stage 1 holds three (TY + 2) x
+// (TX + 4) tiles (phi, psi, omega); stage 2 a (TY + 4) x (TX + 12) phi tile
+// and a (TY + 2) x (TX + 12) mu tile.
+__host__ __device__ constexpr size_t stencil1_smem_bytes(int TX, int TY, size_t real_bytes) {
+  return 3 * (size_t)(TY + 2) * (TX + 4) * real_bytes;
+}
+__host__ __device__ constexpr size_t stencil2_smem_bytes(int TX, int TY, size_t real_bytes) {
+  return (size_t)(2 * TY + 6) * (TX + 12) * real_bytes;
+}
 __host__ __device__ constexpr size_t rowfwd_inst_bytes(int nx, size_t real_bytes) {
   return round128(2 * (size_t)nx * real_bytes + (size_t)padded_len(nx) * 2 * real_bytes);
 }

@@ -176,100 +176,263 @@ __device__ __forceinline__ int persistent_iters(int nitems, int ipc) {
 }
 
 // ============================================================== stencils
-// 2D tiles of TX x TY outputs (TX = min(nx, 128), a template constant so that
-// every tile index is divided by a constant; TY = 8), 256 threads.
-constexpr int kTY = 8;
+// 2D tiles of TX x TY outputs (TX = min(nx, 128), TY = min(ny, 32)); each
+// thread makes a 4 x 4 block of outputs (4 consecutive x in 4 rows), reading
+// its stencil rows from the shared tile with 16-byte loads.  The sign of s
+// selects one of two compiled bodies (the diagonal of Eq. p1y lies on one side).
 
-// stage-1 stencil: inputs phi, psi (and omega) with halo x +-2, y +-1
-template <class T, int TX>
-__global__ void __launch_bounds__(256) k_stencil1(const MemberDesc* __restrict__ descs, int log2nx, int log2ny) {
-  constexpr int W = TX + 4;
-  __shared__ T sh[3][kTY + 2][W];
-  const MemberDesc& D = descs[blockIdx.z];
-  const int nx = 1 << log2nx, ny = 1 << log2ny, mx = nx - 1, my = ny - 1;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * kTY;
-  const bool stokes = D.stokes != 0;
-  const Shear<T> sc(*D.st, false);                      // s^n
-  const T dt = (T)D.dt, inv2h = (T)D.inv_2h;
-  const T* __restrict__ f0 = static_cast<const T*>(D.phi);
-  const T* __restrict__ f1 = static_cast<const T*>(D.psi);
-  const T* __restrict__ f2 = static_cast<const T*>(D.omega);
-  for (int e = threadIdx.x; e < (kTY + 2) * W; e += blockDim.x) {
-    const int r = e / W, c = e - r * W;
-    const size_t g = ((size_t)((y0 - 1 + r) & my) << log2nx) + ((x0 - 2 + c) & mx);
-    sh[0][r][c] = __ldg(f0 + g);
-    sh[1][r][c] = __ldg(f1 + g);
-    if (!stokes) sh[2][r][c] = __ldg(f2 + g);
+// four consecutive reals at a 16-byte-aligned address
+template <class T>
+struct Quad {
+  T v[4];
+};
+__device__ __forceinline__ Quad<float> ld4(const float* p) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  return Quad<float>{{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ Quad<double> ld4(const double* p) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  return Quad<double>{{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ Quad<float> ldg4(const float* p) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  return Quad<float>{{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ Quad<double> ldg4(const double* p) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p)), b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  return Quad<double>{{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st4(float* p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void st4(double* p, double a, double b, double c, double d) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+  reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
+}
+// two reals at an address aligned to two elements
+__device__ __forceinline__ void ldg2(const float* p, float& a, float& b) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  a = v.x;
+  b = v.y;
+}
+__device__ __forceinline__ void ldg2(const double* p, double& a, double& b) {
+  const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  a = v.x;
+  b = v.y;
+}
+__device__ __forceinline__ void st2(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
+__device__ __forceinline__ void st2(double* p, double a, double b) {
+  *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+
+// Eight reals of a tile row, cols c .. c+7 (c a multiple of 4): the stencil
+// row of a 4-point block whose first point sits at c + 2.
+template <class T>
+struct Row8 {
+  T v[8];
+};
+template <class T>
+__device__ __forceinline__ Row8<T> ld8(const T* p) {
+  const Quad<T> a = ld4(p), b = ld4(p + 4);
+  return Row8<T>{{a.v[0], a.v[1], a.v[2], a.v[3], b.v[0], b.v[1], b.v[2], b.v[3]}};
+}
+
+// Derivatives at the 4 points (centre index p + 2) of rows U (j+1), C (j),
+// Dn (j-1): D_x f = (f(i+1) - f(i-1)) / 2h and Eq. p1y's sheared D_y^s f =
+// [w0 (f(i, j+1) - f(i, j-1)) + w1 (f(i+d, j+1) - f(i-d, j-1))] / 2h, with
+// d = -2 for s >= 0 (NEG = false) and d = +2 for s < 0 (NEG = true).
+template <bool NEG, class T>
+__device__ __forceinline__ void grad4(const Row8<T>& U, const Row8<T>& C, const Row8<T>& Dn, T w0, T w1, T inv2h,
+                                      T (&dx)[4], T (&dy)[4]) {
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    dx[p] = (C.v[p + 3] - C.v[p + 1]) * inv2h;
+    const T up = NEG ? U.v[p + 4] : U.v[p];         // f(i+d, j+1)
+    const T dn = NEG ? Dn.v[p] : Dn.v[p + 4];       // f(i-d, j-1)
+    dy[p] = (w0 * (U.v[p + 2] - Dn.v[p + 2]) + w1 * (up - dn)) * inv2h;
   }
-  __syncthreads();
-  T* phis = static_cast<T*>(D.phi_star);
-  T* oms = static_cast<T*>(D.omega_star);
-  const bool wrap = D.remap && sc.dK != 0;
-  for (int e = threadIdx.x; e < kTY * TX; e += blockDim.x) {
-    const int ly = e / TX, lx = e - ly * TX;
-    const int r = ly + 1, c = lx + 2;
-    const int y = y0 + ly, x = x0 + lx;
-    auto dxf = [&](int f) { return (sh[f][r][c + 1] - sh[f][r][c - 1]) * inv2h; };
-    auto dyf = [&](int f) {
-      return (sc.w0 * (sh[f][r + 1][c] - sh[f][r - 1][c]) +
-              sc.w1 * (sh[f][r + 1][c + sc.d] - sh[f][r - 1][c - sc.d])) * inv2h;
-    };
-    const T dxpsi = dxf(1), dypsi = dyf(1);
-    const T pc = sh[0][r][c];
-    phis[((size_t)y << log2nx) + x] = pc - dt * (dypsi * dxf(0) - dxpsi * dyf(0));
-    if (!stokes) {
-      const T ws = sh[2][r][c] - dt * (dypsi * dxf(2) - dxpsi * dyf(2));
-      const int sh_y = wrap ? remap_shift(sc.dK, D.ratio, y, nx) : 0;
-      oms[((size_t)y << log2nx) + ((x + sh_y) & mx)] = ws;
+}
+
+// Fill rows [0, H) of NF tiles (tile column c <-> x0 - OFF + c, OFF = 2 or 6,
+// width TX + 2 OFF) from NF fields at rows y0 - HY + r (periodic).  Interior
+// quads are 16-byte global loads; the OFF halo columns on each side are pairs.
+template <class T, int TX, int OFF, int H, int NF>
+__device__ __forceinline__ void fill_tiles(T* tile, const T* const* src, int x0, int yb, int log2nx, int my,
+                                           int tid, int nthr) {
+  constexpr int QX = TX / 4, W = TX + 2 * OFF, HP = OFF / 2;   // HP halo pairs per side
+  constexpr int SLOTS = QX + 2 * HP;
+  const int mx = (1 << log2nx) - 1;
+  for (int e = tid; e < NF * H * SLOTS; e += nthr) {
+    const int f = e / (H * SLOTS);
+    const int rem = e - f * (H * SLOTS);
+    const int r = rem / SLOTS, k = rem - r * SLOTS;
+    const T* row = src[f] + ((size_t)((yb + r) & my) << log2nx);
+    T* trow = tile + ((size_t)f * H + r) * W;
+    if (k < QX) {
+      const Quad<T> q = ldg4(row + x0 + 4 * k);
+      T* d = trow + OFF + 4 * k;
+      if (OFF % 4 == 0) {
+        st4(d, q.v[0], q.v[1], q.v[2], q.v[3]);
+      } else {
+        st2(d, q.v[0], q.v[1]);
+        st2(d + 2, q.v[2], q.v[3]);
+      }
+    } else {
+      const int h = k - QX;                               // 0 .. 2 HP - 1
+      const int side = h / HP, j = h - side * HP;         // left (0) or right (1) halo, pair j
+      const int c = side == 0 ? 2 * j : OFF + TX + 2 * j;
+      const int x = (x0 - OFF + c) & mx;                  // even, so the pair is contiguous
+      T a, b;
+      ldg2(row + x, a, b);
+      st2(trow + c, a, b);
     }
   }
 }
 
-// stage-2 stencil: mu on a halo tile (x +-2, y +-1) from phi (x +-3, y +-2),
-// then g = c_force (d_x phi d_y mu - d_y phi d_x mu)
-template <class T, int TX>
-__global__ void __launch_bounds__(256) k_stencil2(const MemberDesc* __restrict__ descs, int log2nx, int log2ny) {
-  constexpr int WP = TX + 6, WM = TX + 4;
-  __shared__ T sp[kTY + 4][WP];
-  __shared__ T sm[kTY + 2][WM];
+// stage-1 stencil: phi* = phi - dt J(psi, phi), omega* = omega - dt J(psi, omega)
+// (Eq. advective with J(A, B) = D_y^s A D_x B - D_x A D_y^s B), tiles of
+// phi, psi (and omega) with halo x +-2, y +-1.  At a wrap omega* is stored
+// remapped (row j shifted by the wrap's cells).
+template <bool NEG, class T, int TX, int TY>
+__device__ __forceinline__ void stencil1_body(const MemberDesc& D, const T* tiles, const Shear<T>& sc, int x0,
+                                              int y0, int log2nx) {
+  constexpr int QX = TX / 4, W = TX + 4, H = TY + 2;
+  const int nx = 1 << log2nx, mx = nx - 1;
+  const int q = threadIdx.x % QX, g = threadIdx.x / QX;
+  const bool stokes = D.stokes != 0;
+  const bool wrap = D.remap && sc.dK != 0;
+  const T dt = (T)D.dt, inv2h = (T)D.inv_2h;
+  T* phis = static_cast<T*>(D.phi_star);
+  T* oms = static_cast<T*>(D.omega_star);
+  const T* t0 = tiles;                 // phi
+  const T* t1 = tiles + H * W;         // psi
+  const T* t2 = tiles + 2 * H * W;     // omega
+  const int x = x0 + 4 * q;
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    const int tr = 4 * g + 1 + o;      // tile row of output row y0 + 4 g + o
+    const int y = y0 + 4 * g + o;
+    T dxp[4], dyp[4];
+    grad4<NEG>(ld8(t1 + (tr + 1) * W + 4 * q), ld8(t1 + tr * W + 4 * q), ld8(t1 + (tr - 1) * W + 4 * q), sc.w0,
+               sc.w1, inv2h, dxp, dyp);
+    {
+      const Row8<T> C = ld8(t0 + tr * W + 4 * q);
+      T dxf[4], dyf[4];
+      grad4<NEG>(ld8(t0 + (tr + 1) * W + 4 * q), C, ld8(t0 + (tr - 1) * W + 4 * q), sc.w0, sc.w1, inv2h, dxf, dyf);
+      T r[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) r[p] = C.v[p + 2] - dt * (dyp[p] * dxf[p] - dxp[p] * dyf[p]);
+      st4(phis + ((size_t)y << log2nx) + x, r[0], r[1], r[2], r[3]);
+    }
+    if (!stokes) {
+      const Row8<T> C = ld8(t2 + tr * W + 4 * q);
+      T dxf[4], dyf[4];
+      grad4<NEG>(ld8(t2 + (tr + 1) * W + 4 * q), C, ld8(t2 + (tr - 1) * W + 4 * q), sc.w0, sc.w1, inv2h, dxf, dyf);
+      T r[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) r[p] = C.v[p + 2] - dt * (dyp[p] * dxf[p] - dxp[p] * dyf[p]);
+      T* orow = oms + ((size_t)y << log2nx);
+      if (!wrap) {
+        st4(orow + x, r[0], r[1], r[2], r[3]);
+      } else {
+        const int sh_y = remap_shift(sc.dK, D.ratio, y, nx);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) orow[(x + p + sh_y) & mx] = r[p];
+      }
+    }
+  }
+}
+
+template <class T, int TX, int TY>
+__global__ void __launch_bounds__(256) k_stencil1(const MemberDesc* __restrict__ descs, int log2nx, int log2ny) {
+  constexpr int H = TY + 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];   // stencil1_smem_bytes
+  T* tiles = reinterpret_cast<T*>(smem_raw);
   const MemberDesc& D = descs[blockIdx.z];
-  const int nx = 1 << log2nx, ny = 1 << log2ny, mx = nx - 1, my = ny - 1;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * kTY;
-  const Shear<T> sc(*D.st, true);                        // s^{n+1}
+  const int my = (1 << log2ny) - 1;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const Shear<T> sc(*D.st, false);                      // s^n
+  const T* src[3] = {static_cast<const T*>(D.phi), static_cast<const T*>(D.psi), static_cast<const T*>(D.omega)};
+  if (D.stokes) fill_tiles<T, TX, 2, H, 2>(tiles, src, x0, y0 - 1, log2nx, my, threadIdx.x, blockDim.x);
+  else fill_tiles<T, TX, 2, H, 3>(tiles, src, x0, y0 - 1, log2nx, my, threadIdx.x, blockDim.x);
+  __syncthreads();
+  if (sc.d > 0) stencil1_body<true, T, TX, TY>(D, tiles, sc, x0, y0, log2nx);
+  else stencil1_body<false, T, TX, TY>(D, tiles, sc, x0, y0, log2nx);
+}
+
+// stage-2 stencil: mu = -a phi + b phi^3 - kappa L_s phi (Appendix B item 2:
+// 3-point second differences, 4-point cross difference) on a tile with halo
+// x +-2, y +-1 from phi (halo x +-6 loaded, y +-2), then
+// g = c_force (D_x phi D_y^s mu - D_y^s phi D_x mu) (Eqs. vortNum, G).
+template <bool NEG, class T, int TX, int TY>
+__device__ __forceinline__ void stencil2_body(const MemberDesc& D, const T* tp, T* tm, const Shear<T>& sc, int x0,
+                                              int y0, int log2nx) {
+  constexpr int QX = TX / 4, W = TX + 12, HP = TY + 4, HM = TY + 2;
+  constexpr int NQ = QX + 1;                  // mu quads per row: tile cols 4 .. TX + 7
+  const int tid = threadIdx.x, nthr = blockDim.x;
   const T a = (T)D.a, b = (T)D.b, kappa = (T)D.kappa;
-  const T inv2h = (T)D.inv_2h, ih2 = (T)D.inv_h2, i4h2 = (T)D.inv_4h2;
+  const T ih2 = (T)D.inv_h2, i4h2 = (T)D.inv_4h2, inv2h = (T)D.inv_2h;
   const T cxx = T(1) + sc.s * sc.s, cxy = T(2) * sc.s;
+  // mu tile row rm <-> y0 - 1 + rm <-> phi tile row rm + 1; mu quad at tile col 4 (k + 1)
+  for (int e = tid; e < HM * NQ; e += nthr) {
+    const int rm = e / NQ, k = e - rm * NQ;
+    const int c = 4 * (k + 1);
+    const T* pr = tp + (rm + 1) * W;
+    const Quad<T> Cl = ld4(pr + c - 4), Cc = ld4(pr + c), Cr = ld4(pr + c + 4);
+    const Quad<T> Ul = ld4(pr + W + c - 4), Uc = ld4(pr + W + c), Ur = ld4(pr + W + c + 4);
+    const Quad<T> Dl = ld4(pr - W + c - 4), Dc = ld4(pr - W + c), Dr = ld4(pr - W + c + 4);
+    const T cw[6] = {Cl.v[3], Cc.v[0], Cc.v[1], Cc.v[2], Cc.v[3], Cr.v[0]};
+    const T uw[6] = {Ul.v[3], Uc.v[0], Uc.v[1], Uc.v[2], Uc.v[3], Ur.v[0]};
+    const T dw[6] = {Dl.v[3], Dc.v[0], Dc.v[1], Dc.v[2], Dc.v[3], Dr.v[0]};
+    T m[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      const T pc = cw[p + 1];
+      const T dxx = (cw[p + 2] - T(2) * pc + cw[p]) * ih2;
+      const T dyy = (uw[p + 1] - T(2) * pc + dw[p + 1]) * ih2;
+      const T dxy = (uw[p + 2] - dw[p + 2] - uw[p] + dw[p]) * i4h2;
+      const T lap = cxx * dxx - cxy * dxy + dyy;
+      m[p] = -a * pc + b * ((pc * pc) * pc) - kappa * lap;
+    }
+    st4(tm + rm * W + c, m[0], m[1], m[2], m[3]);
+  }
+  __syncthreads();
+  const int q = tid % QX, g = tid / QX;
   const T cf = (T)D.c_force;
-  const T* __restrict__ phi = static_cast<const T*>(D.phi);
-  for (int e = threadIdx.x; e < (kTY + 4) * WP; e += blockDim.x) {
-    const int r = e / WP, c = e - r * WP;
-    sp[r][c] = __ldg(phi + ((size_t)((y0 - 2 + r) & my) << log2nx) + ((x0 - 3 + c) & mx));
+  T* gout = static_cast<T*>(D.gbuf);
+  const int x = x0 + 4 * q;
+  // the 8-wide rows of output block (cols x - 2 .. x + 5) start at tile col 4 q + 4
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    const int y = y0 + 4 * g + o;
+    const int rp = 4 * g + 2 + o, rmu = 4 * g + 1 + o;   // phi and mu tile rows of y
+    T dxp[4], dyp[4], dxm[4], dym[4];
+    grad4<NEG>(ld8(tp + (rp + 1) * W + 4 * q + 4), ld8(tp + rp * W + 4 * q + 4), ld8(tp + (rp - 1) * W + 4 * q + 4),
+               sc.w0, sc.w1, inv2h, dxp, dyp);
+    grad4<NEG>(ld8(tm + (rmu + 1) * W + 4 * q + 4), ld8(tm + rmu * W + 4 * q + 4),
+               ld8(tm + (rmu - 1) * W + 4 * q + 4), sc.w0, sc.w1, inv2h, dxm, dym);
+    T r[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) r[p] = cf * (dxp[p] * dym[p] - dyp[p] * dxm[p]);
+    st4(gout + ((size_t)y << log2nx) + x, r[0], r[1], r[2], r[3]);
   }
+}
+
+template <class T, int TX, int TY>
+__global__ void __launch_bounds__(256) k_stencil2(const MemberDesc* __restrict__ descs, int log2nx, int log2ny) {
+  constexpr int W = TX + 12, HP = TY + 4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];   // stencil2_smem_bytes
+  T* tp = reinterpret_cast<T*>(smem_raw);                     // phi tile, HP x W
+  T* tm = tp + HP * W;                                        // mu tile, (TY + 2) x W
+  const MemberDesc& D = descs[blockIdx.z];
+  const int my = (1 << log2ny) - 1;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const Shear<T> sc(*D.st, true);                       // s^{n+1}
+  const T* src[1] = {static_cast<const T*>(D.phi)};
+  fill_tiles<T, TX, 6, HP, 1>(tp, src, x0, y0 - 2, log2nx, my, threadIdx.x, blockDim.x);
   __syncthreads();
-  // mu (Appendix B item 2: 3-point second differences, 4-point cross difference)
-  for (int e = threadIdx.x; e < (kTY + 2) * WM; e += blockDim.x) {
-    const int r = e / WM, c = e - r * WM;
-    const int pr = r + 1, pcc = c + 1;
-    const T pc = sp[pr][pcc];
-    const T dxx = (sp[pr][pcc + 1] - T(2) * pc + sp[pr][pcc - 1]) * ih2;
-    const T dyy = (sp[pr + 1][pcc] - T(2) * pc + sp[pr - 1][pcc]) * ih2;
-    const T dxy = (sp[pr + 1][pcc + 1] - sp[pr - 1][pcc + 1] - sp[pr + 1][pcc - 1] + sp[pr - 1][pcc - 1]) * i4h2;
-    const T lap = cxx * dxx - cxy * dxy + dyy;
-    sm[r][c] = -a * pc + b * ((pc * pc) * pc) - kappa * lap;
-  }
-  __syncthreads();
-  T* g = static_cast<T*>(D.gbuf);
-  for (int e = threadIdx.x; e < kTY * TX; e += blockDim.x) {
-    const int ly = e / TX, lx = e - ly * TX;
-    const int rp = ly + 2, cp = lx + 3, rm = ly + 1, cm = lx + 2;
-    const T dxphi = (sp[rp][cp + 1] - sp[rp][cp - 1]) * inv2h;
-    const T dyphi = (sc.w0 * (sp[rp + 1][cp] - sp[rp - 1][cp]) +
-                     sc.w1 * (sp[rp + 1][cp + sc.d] - sp[rp - 1][cp - sc.d])) * inv2h;
-    const T dxmu = (sm[rm][cm + 1] - sm[rm][cm - 1]) * inv2h;
-    const T dymu = (sc.w0 * (sm[rm + 1][cm] - sm[rm - 1][cm]) +
-                    sc.w1 * (sm[rm + 1][cm + sc.d] - sm[rm - 1][cm - sc.d])) * inv2h;
-    g[((size_t)(y0 + ly) << log2nx) + x0 + lx] = cf * (dxphi * dymu - dyphi * dxmu);
-  }
+  if (sc.d > 0) stencil2_body<true, T, TX, TY>(D, tp, tm, sc, x0, y0, log2nx);
+  else stencil2_body<false, T, TX, TY>(D, tp, tm, sc, x0, y0, log2nx);
 }
 
 // ====================================================== forward row transforms
@@ -725,17 +888,50 @@ void launch_step_state_init(const MemberDesc* d, int nmem, cudaStream_t st) {
   k_step_state_init<<<(nmem + 127) / 128, 128, 0, st>>>(d, nmem);
 }
 
+// stencil tiles: TX = min(nx, 128) columns, TY = min(ny, 32) rows,
+// (TX / 4) (TY / 4) threads
+template <class T, int TX, int TY>
+void launch_stencil_t(int which, const MemberDesc* d, int nmem, int log2nx, int log2ny, const LaunchCfg& c,
+                      cudaStream_t st) {
+  const dim3 grid(c.grid_x, c.grid_y, nmem);
+  if (which == 0) k_stencil1<T, TX, TY><<<grid, c.threads, c.smem, st>>>(d, log2nx, log2ny);
+  else k_stencil2<T, TX, TY><<<grid, c.threads, c.smem, st>>>(d, log2nx, log2ny);
+}
+template <class T, int TX, int TY>
+void stencil_smem_limits_t(int lim) {
+  cudaFuncSetAttribute(k_stencil1<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  cudaFuncSetAttribute(k_stencil2<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+}
+template <class T, int TY>
+void stencil_smem_limits_ty(int lim) {
+  stencil_smem_limits_t<T, 16, TY>(lim);
+  stencil_smem_limits_t<T, 32, TY>(lim);
+  stencil_smem_limits_t<T, 64, TY>(lim);
+  stencil_smem_limits_t<T, 128, TY>(lim);
+}
+template <class T, int TY>
+void launch_stencil_ty(int which, const MemberDesc* d, int nmem, int log2nx, int log2ny, const LaunchCfg& c,
+                       cudaStream_t st) {
+  switch (log2nx) {
+    case 4: launch_stencil_t<T, 16, TY>(which, d, nmem, log2nx, log2ny, c, st); break;
+    case 5: launch_stencil_t<T, 32, TY>(which, d, nmem, log2nx, log2ny, c, st); break;
+    case 6: launch_stencil_t<T, 64, TY>(which, d, nmem, log2nx, log2ny, c, st); break;
+    default: launch_stencil_t<T, 128, TY>(which, d, nmem, log2nx, log2ny, c, st); break;
+  }
+}
+template <class T>
+void launch_stencil(int which, const MemberDesc* d, int nmem, int log2nx, int log2ny, const LaunchCfg& c,
+                    cudaStream_t st) {
+  if (log2ny >= 5) launch_stencil_ty<T, 32>(which, d, nmem, log2nx, log2ny, c, st);
+  else launch_stencil_ty<T, 16>(which, d, nmem, log2nx, log2ny, c, st);
+}
+
 template <class T>
 void launch_step_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int log2ny, const cplx<T>* tw,
                         const LaunchCfg& c, cudaStream_t st) {
   switch (kind) {
     case KIND_STENCIL1:
-      switch (log2nx) {
-        case 4: k_stencil1<T, 16><<<dim3(c.grid_x, c.grid_y, nmem), c.threads, 0, st>>>(d, log2nx, log2ny); break;
-        case 5: k_stencil1<T, 32><<<dim3(c.grid_x, c.grid_y, nmem), c.threads, 0, st>>>(d, log2nx, log2ny); break;
-        case 6: k_stencil1<T, 64><<<dim3(c.grid_x, c.grid_y, nmem), c.threads, 0, st>>>(d, log2nx, log2ny); break;
-        default: k_stencil1<T, 128><<<dim3(c.grid_x, c.grid_y, nmem), c.threads, 0, st>>>(d, log2nx, log2ny); break;
-      }
+      launch_stencil<T>(0, d, nmem, log2nx, log2ny, c, st);
       break;
     case KIND_ROWFWD_PHI:
       k_rowfwd<T><<<dim3(c.grid_x, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw, 0);
@@ -750,12 +946,7 @@ void launch_step_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int
       k_rowinv<T><<<dim3(c.grid_x, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw, 0);
       break;
     case KIND_STENCIL2:
-      switch (log2nx) {
-        case 4: k_stencil2<T, 16><<<dim3(c.grid_x, c.grid_y, nmem), c.threads, 0, st>>>(d, log2nx, log2ny); break;
-        case 5: k_stencil2<T, 32><<<dim3(c.grid_x, c.grid_y, nmem), c.threads, 0, st>>>(d, log2nx, log2ny); break;
-        case 6: k_stencil2<T, 64><<<dim3(c.grid_x, c.grid_y, nmem), c.threads, 0, st>>>(d, log2nx, log2ny); break;
-        default: k_stencil2<T, 128><<<dim3(c.grid_x, c.grid_y, nmem), c.threads, 0, st>>>(d, log2nx, log2ny); break;
-      }
+      launch_stencil<T>(1, d, nmem, log2nx, log2ny, c, st);
       break;
     case KIND_ROWFWD_G:
       k_rowfwd<T><<<dim3(c.grid_x, nmem), c.threads, c.smem, st>>>(d, log2nx, log2ny, tw, 1);
@@ -796,6 +987,8 @@ void set_step_smem_limits() {
   cudaFuncSetAttribute(k_rowfwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   cudaFuncSetAttribute(k_colpass<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
   if (sizeof(T) == 4) cudaFuncSetAttribute(k_colpass_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+  stencil_smem_limits_ty<T, 16>(lim);
+  stencil_smem_limits_ty<T, 32>(lim);
   cudaFuncSetAttribute(k_rowinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
