@@ -185,13 +185,33 @@ __host__ __device__ constexpr int padded_len(int N) { return N + N / 16; }
 // Per-stage twiddle tables.  A stage of radix R = 2^LR after sub-transforms of
 // length Ns = 2^a multiplies input r of butterfly k = j mod Ns by W_L^{k r},
 // L = Ns R.  The table stores exp(+2 pi i k r / L) at
-// [stage_table_offset(a, LR) + k R + r], r = 0..R-1, so a thread reads its R
-// factors as contiguous 16-byte vectors and a warp reads contiguous rows.
+// [stage_table_offset(a, LR) + (r / 2) 2 Ns + 2 k + r % 2], r = 0..R-1: a
+// thread reads the factors r, r+1 as one 16-byte vector (FP32) and, for each
+// r / 2, the threads of a warp (consecutive k) read one contiguous run.
 // Blocks for a = 1..11, LR = 1..4 (only those with a + LR <= 12 are used).
 __host__ __device__ constexpr int stage_table_offset(int a, int LR) {
   return 30 * ((1 << a) - 2) + (1 << a) * ((1 << LR) - 2);
 }
 __host__ __device__ constexpr int stage_table_len() { return 30 * ((1 << 12) - 2); }
+
+// the R factors of butterfly k from its stage-table block (layout above)
+template <int R>
+__device__ __forceinline__ void load_stage_factors(const float2* __restrict__ blk, int k, int Ns, float2 (&f)[R]) {
+#pragma unroll
+  for (int h = 0; h < R / 2; ++h) {
+    const float4 x = __ldg(reinterpret_cast<const float4*>(blk + h * 2 * Ns + 2 * k));
+    f[2 * h] = float2{x.x, x.y};
+    f[2 * h + 1] = float2{x.z, x.w};
+  }
+}
+template <int R>
+__device__ __forceinline__ void load_stage_factors(const double2* __restrict__ blk, int k, int Ns, double2 (&f)[R]) {
+#pragma unroll
+  for (int h = 0; h < R / 2; ++h) {
+    f[2 * h] = __ldg(blk + h * 2 * Ns + 2 * k);
+    f[2 * h + 1] = __ldg(blk + h * 2 * Ns + 2 * k + 1);
+  }
+}
 
 template <bool INV, int LR, class C>
 __device__ __forceinline__ void dft_radix(C* v) {
@@ -218,21 +238,8 @@ __device__ __forceinline__ void fft_reg_stage(C (&v)[kP], int log2N, int log2Ns,
 #pragma unroll
     for (int r = 0; r < R; ++r) w[r] = v[b + r * B];
     if (log2Ns > 0) {
-      // the R factors of this butterfly: one contiguous row of the stage table
-      const C* row = twt + stage_table_offset(log2Ns, LR) + k * R;
       C f[R];
-      if (sizeof(C) == 8) {
-        const float4* r4 = reinterpret_cast<const float4*>(row);
-#pragma unroll
-        for (int h = 0; h < R / 2; ++h) {
-          const float4 x = __ldg(r4 + h);
-          f[2 * h] = C{x.x, x.y};
-          f[2 * h + 1] = C{x.z, x.w};
-        }
-      } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) f[r] = __ldg(row + r);
-      }
+      load_stage_factors<R>(twt + stage_table_offset(log2Ns, LR), k, Ns, f);
 #pragma unroll
       for (int r = 1; r < R; ++r) w[r] = cmul(w[r], INV ? f[r] : cconj(f[r]));
     }
@@ -295,14 +302,8 @@ __device__ __forceinline__ void fft_reg2_stage(float2 (&a)[kP], float2 (&b)[kP],
       wb[r] = b[bb + r * B];
     }
     if (log2Ns > 0) {
-      const float4* r4 = reinterpret_cast<const float4*>(twt + stage_table_offset(log2Ns, LR) + k * R);
       C f[R];
-#pragma unroll
-      for (int h = 0; h < R / 2; ++h) {
-        const float4 x = __ldg(r4 + h);
-        f[2 * h] = C{x.x, x.y};
-        f[2 * h + 1] = C{x.z, x.w};
-      }
+      load_stage_factors<R>(twt + stage_table_offset(log2Ns, LR), k, Ns, f);
 #pragma unroll
       for (int r = 1; r < R; ++r) {
         const C fr = INV ? f[r] : cconj(f[r]);

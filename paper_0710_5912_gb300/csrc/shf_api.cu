@@ -421,8 +421,9 @@ int build(shf_grid* g, const std::vector<int>& nx, const std::vector<int>& ny, c
     if (rc) return rc;
   }
   // twiddle table W[k] = exp(2 pi i k / NMAX) and the register FFT's stage
-  // tables (entry (log2Ns, LR, k, r) = exp(2 pi i k r / (Ns R))), both computed
-  // in double and rounded once to the working precision
+  // tables (entry (log2Ns, LR, k, r) = exp(2 pi i k r / (Ns R)) at offset
+  // (r / 2) 2 Ns + 2 k + r % 2 of its block), both computed in double and
+  // rounded once to the working precision
   std::vector<double> tw(2 * NMAX);
   for (int k = 0; k < NMAX; ++k) unit_root(k, NMAX, &tw[2 * k], &tw[2 * k + 1]);
   std::vector<double> twr(2 * (size_t)stage_table_len());
@@ -431,7 +432,7 @@ int build(shf_grid* g, const std::vector<int>& nx, const std::vector<int>& ny, c
       const long Ns = 1L << a, R = 1L << lr, L = Ns * R;
       for (long k = 0; k < Ns; ++k)
         for (long r = 0; r < R; ++r) {
-          const size_t e = (size_t)stage_table_offset(a, lr) + k * R + r;
+          const size_t e = (size_t)stage_table_offset(a, lr) + (r / 2) * 2 * Ns + 2 * k + r % 2;
           unit_root((k * r) % L, L, &twr[2 * e], &twr[2 * e + 1]);
         }
     }
