@@ -184,32 +184,43 @@ __host__ __device__ constexpr int padded_len(int N) { return N + N / 16; }
 
 // Per-stage twiddle tables.  A stage of radix R = 2^LR after sub-transforms of
 // length Ns = 2^a multiplies input r of butterfly k = j mod Ns by W_L^{k r},
-// L = Ns R.  The table stores exp(+2 pi i k r / L) at
-// [stage_table_offset(a, LR) + (r / 2) 2 Ns + 2 k + r % 2], r = 0..R-1: a
-// thread reads the factors r, r+1 as one 16-byte vector (FP32) and, for each
-// r / 2, the threads of a warp (consecutive k) read one contiguous run.
-// Blocks for a = 1..11, LR = 1..4 (only those with a + LR <= 12 are used).
+// L = Ns R.  The table holds, for each (a, LR) with a + LR <= 12, the pair
+// (exp(+2 pi i k / L), exp(+2 pi i 2k / L)) for k = 0..Ns-1 at entries
+// [2 (stage_table_offset(a, LR) + k)], [.. + 1]: one 16-byte load (FP32) per
+// butterfly, and the warp's loads are one contiguous run.  The other factors
+// are products of these two (at most two roundings deep): w3 = w1 w2,
+// w4 = w2 w2, w5 = w4 w1, w6 = w4 w2, w7 = w4 w3.
 __host__ __device__ constexpr int stage_table_offset(int a, int LR) {
-  return 30 * ((1 << a) - 2) + (1 << a) * ((1 << LR) - 2);
+  return 4 * ((1 << a) - 1) + (LR - 1) * (1 << a);
 }
-__host__ __device__ constexpr int stage_table_len() { return 30 * ((1 << 12) - 2); }
+// complex entries of the whole table (pairs for a = 0..11, LR = 1..4)
+__host__ __device__ constexpr int stage_table_len() { return 2 * 4 * ((1 << 12) - 1); }
 
-// the R factors of butterfly k from its stage-table block (layout above)
-template <int R>
-__device__ __forceinline__ void load_stage_factors(const float2* __restrict__ blk, int k, int Ns, float2 (&f)[R]) {
-#pragma unroll
-  for (int h = 0; h < R / 2; ++h) {
-    const float4 x = __ldg(reinterpret_cast<const float4*>(blk + h * 2 * Ns + 2 * k));
-    f[2 * h] = float2{x.x, x.y};
-    f[2 * h + 1] = float2{x.z, x.w};
-  }
+__device__ __forceinline__ void load_pair(const float2* __restrict__ p, float2& w1, float2& w2) {
+  const float4 x = __ldg(reinterpret_cast<const float4*>(p));
+  w1 = float2{x.x, x.y};
+  w2 = float2{x.z, x.w};
 }
-template <int R>
-__device__ __forceinline__ void load_stage_factors(const double2* __restrict__ blk, int k, int Ns, double2 (&f)[R]) {
-#pragma unroll
-  for (int h = 0; h < R / 2; ++h) {
-    f[2 * h] = __ldg(blk + h * 2 * Ns + 2 * k);
-    f[2 * h + 1] = __ldg(blk + h * 2 * Ns + 2 * k + 1);
+__device__ __forceinline__ void load_pair(const double2* __restrict__ p, double2& w1, double2& w2) {
+  w1 = __ldg(p);
+  w2 = __ldg(p + 1);
+}
+
+// the R factors W_L^{k r}, r = 0..R-1, of butterfly k of a stage
+template <int R, class C>
+__device__ __forceinline__ void load_stage_factors(const C* __restrict__ tab, int log2Ns, int LR, int k, C (&f)[R]) {
+  C w1, w2;
+  load_pair(tab + 2 * (stage_table_offset(log2Ns, LR) + k), w1, w2);
+  f[1] = w1;
+  if (R > 2) {
+    f[2] = w2;
+    f[3] = cmul(w1, w2);
+  }
+  if (R > 4) {
+    f[4] = cmul(w2, w2);
+    f[5] = cmul(f[4], w1);
+    f[6] = cmul(f[4], w2);
+    f[7] = cmul(f[4], f[3]);
   }
 }
 
@@ -239,7 +250,7 @@ __device__ __forceinline__ void fft_reg_stage(C (&v)[kP], int log2N, int log2Ns,
     for (int r = 0; r < R; ++r) w[r] = v[b + r * B];
     if (log2Ns > 0) {
       C f[R];
-      load_stage_factors<R>(twt + stage_table_offset(log2Ns, LR), k, Ns, f);
+      load_stage_factors<R>(twt, log2Ns, LR, k, f);
 #pragma unroll
       for (int r = 1; r < R; ++r) w[r] = cmul(w[r], INV ? f[r] : cconj(f[r]));
     }
@@ -303,7 +314,7 @@ __device__ __forceinline__ void fft_reg2_stage(float2 (&a)[kP], float2 (&b)[kP],
     }
     if (log2Ns > 0) {
       C f[R];
-      load_stage_factors<R>(twt + stage_table_offset(log2Ns, LR), k, Ns, f);
+      load_stage_factors<R>(twt, log2Ns, LR, k, f);
 #pragma unroll
       for (int r = 1; r < R; ++r) {
         const C fr = INV ? f[r] : cconj(f[r]);

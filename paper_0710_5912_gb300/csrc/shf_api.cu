@@ -421,20 +421,20 @@ int build(shf_grid* g, const std::vector<int>& nx, const std::vector<int>& ny, c
     if (rc) return rc;
   }
   // twiddle table W[k] = exp(2 pi i k / NMAX) and the register FFT's stage
-  // tables (entry (log2Ns, LR, k, r) = exp(2 pi i k r / (Ns R)) at offset
-  // (r / 2) 2 Ns + 2 k + r % 2 of its block), both computed in double and
-  // rounded once to the working precision
+  // tables (for each stage and butterfly k, exp(2 pi i k / L) and
+  // exp(2 pi i 2k / L), L = Ns R), both computed in double and rounded once
+  // to the working precision
   std::vector<double> tw(2 * NMAX);
   for (int k = 0; k < NMAX; ++k) unit_root(k, NMAX, &tw[2 * k], &tw[2 * k + 1]);
   std::vector<double> twr(2 * (size_t)stage_table_len());
-  for (int a = 1; a <= 11; ++a)
+  for (int a = 1; a <= 11; ++a)              // a = 0 (Ns = 1) needs no factors
     for (int lr = 1; lr <= 4 && a + lr <= LOG2_NMAX; ++lr) {
-      const long Ns = 1L << a, R = 1L << lr, L = Ns * R;
-      for (long k = 0; k < Ns; ++k)
-        for (long r = 0; r < R; ++r) {
-          const size_t e = (size_t)stage_table_offset(a, lr) + (r / 2) * 2 * Ns + 2 * k + r % 2;
-          unit_root((k * r) % L, L, &twr[2 * e], &twr[2 * e + 1]);
-        }
+      const long Ns = 1L << a, L = Ns << lr;
+      for (long k = 0; k < Ns; ++k) {
+        const size_t e = 2 * ((size_t)stage_table_offset(a, lr) + k);
+        unit_root(k % L, L, &twr[2 * e], &twr[2 * e + 1]);
+        unit_root((2 * k) % L, L, &twr[2 * e + 2], &twr[2 * e + 3]);
+      }
     }
   auto upload = [&](void** dst, const std::vector<double>& src) -> int {
     const size_t cnt = src.size() / 2;
