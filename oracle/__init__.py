@@ -13,5 +13,5 @@ from .scheme import (  # noqa: F401
     lap_sheared, bracket, chemical_potential, body_force_curl, wavenumbers,
     sheared_k2, remap_rows, advect, cahn_hilliard_spectral, vorticity_poisson_solve,
     stokes_solve, flow_substep, step, run,
-    mean_phi, structure_factor_moments, structure_factor_binned,
+    mean_phi, structure_factor_moments, structure_factor_binned, gradient_tensor, principal_lengths,
 )

@@ -318,6 +318,37 @@ def structure_factor_moments(phi, s: float, dx: float = 1.0):
     return S0, S1, Sm1, L1, Ls
 
 
+def gradient_tensor(phi, s: float, dx: float = 1.0):
+    """The anisotropy tensor of Eq. L_matrix without its prefactor l:
+    G_ab = int d_a phi d_b phi / int phi^2 with laboratory derivatives
+    (d_x, d_y - s d_x) of the trigonometric interpolant, i.e. by Parseval
+    G_ab = sum q_ca q_cb |phi_hat|^2 / sum |phi_hat|^2 over the modes off the
+    Nyquist lines (k = 0 included in the denominator), q_c = (q_x, q_y - s q_x).
+    Returns (G_xx, G_xy, G_yy)."""
+    ny, nx = phi.shape
+    QX, QY, nyq = wavenumbers(nx, ny, dx)
+    KY = QY - s * QX
+    P = np.abs(fft2(phi)) ** 2
+    P[nyq] = 0.0
+    den = math.fsum(P.ravel().tolist())
+    gxx = math.fsum((QX * QX * P).ravel().tolist()) / den
+    gxy = math.fsum((QX * KY * P).ravel().tolist()) / den
+    gyy = math.fsum((KY * KY * P).ravel().tolist()) / den
+    return gxx, gxy, gyy
+
+
+def principal_lengths(G, ell: float):
+    """L_par, L_perp of Eq. L_matrix: the reciprocals of the eigenvalues of
+    D = ell G (smallest eigenvalue -> the long axis L_par); infinite where an
+    eigenvalue is zero."""
+    gxx, gxy, gyy = G
+    half_tr = 0.5 * (gxx + gyy)
+    rad = math.hypot(0.5 * (gxx - gyy), gxy)
+    lam_max, lam_min = half_tr + rad, half_tr - rad
+    inv = lambda lam: 1.0 / (ell * lam) if lam > 0 else float("inf")
+    return inv(lam_min), inv(lam_max)
+
+
 def structure_factor_binned(phi, s: float, nbins: int, dx: float = 1.0):
     """Radially binned S: bin b sums S over the kept modes (as in
     structure_factor_moments) with b <= k / dk < b + 1, where the bin width is

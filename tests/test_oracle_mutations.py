@@ -101,6 +101,14 @@ def _mut_vort_cn_sign(omega_star, F, s, p, QX, QY, nyquist):
     return np.real(np.fft.ifft2(Psi)), np.real(np.fft.ifft2(W_new))
 
 
+def _mut_tensor_unsheared(phi, s, dx=1.0):
+    # laboratory y-derivative taken as the plain co-sheared d_y (tilt dropped)
+    return _orig_gradient_tensor(phi, 0.0, dx)
+
+
+_orig_gradient_tensor = scheme.gradient_tensor
+
+
 def _run_first_failing(checks):
     for fn in checks:
         try:
@@ -133,6 +141,8 @@ MUTATIONS = {
                   [lambda: tsp.test_stokes_solve_matches_dense_biharmonic(0.0, (8, 8))]),
     "vort_cn_sign": ("vorticity_poisson_solve", _mut_vort_cn_sign,
                      [lambda: tsp.test_vorticity_and_poisson_match_dense_solve(0.3)]),
+    "tensor_unsheared": ("gradient_tensor", _mut_tensor_unsheared,
+                         [tstep.test_gradient_tensor_matches_analytic_lab_derivatives]),
 }
 
 

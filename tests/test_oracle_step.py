@@ -274,3 +274,52 @@ def test_structure_factor_of_single_mode(s):
 def test_mean_phi_is_correctly_rounded():
     vals = np.array([1e16, 1.0, -1e16, 1.0])
     assert scheme.mean_phi(vals.reshape(2, 2)) == 0.5
+
+
+@pytest.mark.parametrize("s", [0.0, 0.37, -0.5])
+def test_gradient_tensor_of_modes_is_the_closed_form(s):
+    """Eq. L_matrix by Parseval: for orthogonal plane waves a_i cos(theta_i) the
+    tensor is sum a_i^2/2 q_i q_i^T / (c^2 + sum a_i^2/2), with q the laboratory
+    wavevector (q_x, q_y - s q_x) of each co-sheared grid mode and c the mean."""
+    nx, ny, dx = 32, 16, 0.8
+    modes = [(3, 1, 0.7, 0.3), (-2, 3, 0.4, 1.1)]          # (m, n, amplitude, phase)
+    c = 0.25
+    phi = c + sum(inputs.cosine_mode(nx, ny, m, n, amp=a, dx=dx, phase=ph) for m, n, a, ph in modes)
+    G = scheme.gradient_tensor(phi, s, dx)
+    num = np.zeros((2, 2))
+    den = c * c
+    for m, n, a, _ in modes:
+        q = np.array([2 * math.pi * m / (nx * dx), 2 * math.pi * n / (ny * dx) - s * 2 * math.pi * m / (nx * dx)])
+        num += a * a / 2 * np.outer(q, q)
+        den += a * a / 2
+    want = num / den
+    assert np.allclose([G[0], G[1], G[2]], [want[0, 0], want[0, 1], want[1, 1]], rtol=1e-12, atol=1e-14)
+
+
+def test_gradient_tensor_matches_analytic_lab_derivatives():
+    """A smooth lab-frame field f(x, y) sampled on the co-sheared grid at strain s
+    (lab x = x' + s y'): the tensor is the mean of grad f grad f^T over the box
+    divided by the mean of f^2, with the exact derivatives of f."""
+    nx, ny, dx, s = 48, 24, 0.5, 0.375
+    Lx, Ly = nx * dx, ny * dx
+    Xp, Yp = inputs.grid_coords(nx, ny, dx)
+    # f = cos(a x + b y) + 0.5 sin(c x + d y) with (a, b), (c, d) lab wavevectors whose
+    # co-sheared components (a, b + s a) are grid modes
+    a, b = 2 * math.pi * 2 / Lx, 2 * math.pi * 1 / Ly - s * 2 * math.pi * 2 / Lx
+    c, d = 2 * math.pi * -1 / Lx, 2 * math.pi * 3 / Ly - s * 2 * math.pi * -1 / Lx
+    X, Y = Xp + s * Yp, Yp
+    f = np.cos(a * X + b * Y) + 0.5 * np.sin(c * X + d * Y)
+    fx = -a * np.sin(a * X + b * Y) + 0.5 * c * np.cos(c * X + d * Y)
+    fy = -b * np.sin(a * X + b * Y) + 0.5 * d * np.cos(c * X + d * Y)
+    den = np.mean(f * f)
+    want = (np.mean(fx * fx) / den, np.mean(fx * fy) / den, np.mean(fy * fy) / den)
+    assert np.allclose(scheme.gradient_tensor(f, s, dx), want, rtol=1e-12, atol=1e-13)
+
+
+def test_principal_lengths_are_reciprocal_eigenvalues():
+    G = (2.0, 0.5, 1.0)
+    ev = np.linalg.eigvalsh(np.array([[2.0, 0.5], [0.5, 1.0]]))
+    Lpar, Lperp = scheme.principal_lengths(G, 0.5)
+    assert math.isclose(Lpar, 1 / (0.5 * ev[0]), rel_tol=1e-14)
+    assert math.isclose(Lperp, 1 / (0.5 * ev[1]), rel_tol=1e-14)
+    assert scheme.principal_lengths((1.0, 0.0, 0.0), 1.0) == (float("inf"), 1.0)
