@@ -145,6 +145,17 @@ int shf_mass(shf_grid* g, double* mean_phi);
  * with dk = 2 pi / (ny dx). */
 int shf_structure_factor(shf_grid* g, double* S_binned, int nbins, double moments[5]);
 
+/* The anisotropy tensor of Eq. L_matrix (Section III) at the current state:
+ * G = { G_xx, G_xy, G_yy }, G_ab = int d_a phi d_b phi / int phi^2 with the
+ * laboratory derivatives (d_x, d_y - s d_x), evaluated by Parseval on the
+ * modes off the Nyquist lines (k = 0 included in the denominator); units
+ * 1/length^2.  lengths (nullable) = { L_par, L_perp }, the reciprocal
+ * eigenvalues of D = l G with l = sqrt(kappa / a) (the paper's interfacial
+ * width l when a = b = 1, kappa = l^2): L_par from the smaller eigenvalue
+ * (the long principal axis), INFINITY for a zero eigenvalue.
+ * SHF_ESTATE if phi is identically zero. */
+int shf_gradient_tensor(shf_grid* g, double G[3], double lengths[2]);
+
 /* Checkpoint: a header (magic, version, sizes, precision, remap mode,
  * parameters, n, CRC-32 of the payload) and phi, psi, omega in the grid's
  * precision, so that a resumed run is bit-identical to an uninterrupted one.

@@ -165,6 +165,14 @@ def shf_mass(h):
     return m.value
 
 
+def shf_gradient_tensor(h):
+    """((G_xx, G_xy, G_yy), (L_par, L_perp)) of the current state."""
+    G = np.zeros(3)
+    L = np.zeros(2)
+    _check(lib().shf_gradient_tensor(h, _dptr(G), _dptr(L)), h, "shf_gradient_tensor")
+    return tuple(G), tuple(L)
+
+
 def shf_structure_factor(h, nbins=0):
     moments = np.zeros(5)
     bins = np.zeros(max(int(nbins), 1))
@@ -259,6 +267,9 @@ class Grid:
     def structure_factor(self, nbins=0):
         return shf_structure_factor(self.handle, nbins)
 
+    def gradient_tensor(self):
+        return shf_gradient_tensor(self.handle)
+
     def save(self, path):
         shf_save(self.handle, path)
 
@@ -290,6 +301,9 @@ class Member:
 
     def structure_factor(self, nbins=0):
         return shf_structure_factor(self.handle, nbins)
+
+    def gradient_tensor(self):
+        return shf_gradient_tensor(self.handle)
 
     def get_time(self):
         return shf_get_time(self.handle)

@@ -131,6 +131,7 @@ SIGNATURES = {
     "shf_get_time": (c_int, [c_void_p, P_int64, P_double, P_double, P_int64]),
     "shf_mass": (c_int, [c_void_p, P_double]),
     "shf_structure_factor": (c_int, [c_void_p, P_double, c_int, P_double]),
+    "shf_gradient_tensor": (c_int, [c_void_p, P_double, P_double]),
     "shf_save": (c_int, [c_void_p, c_char_p]),
     "shf_load": (c_int, [c_void_p, c_char_p]),
     "shf_create_ensemble": (c_int, [P_void_p, c_int, P_int, P_int, P_double, P_double, P_uint64, c_double,

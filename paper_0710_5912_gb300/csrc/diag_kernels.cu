@@ -118,6 +118,9 @@ __global__ void __launch_bounds__(512) k_sf_rows(const T* __restrict__ f, cplx<T
 // S = |phi_hat|^2 / (nx ny)^2 over the laboratory wavevector magnitude
 // k = |(q_x, q_y - s q_x)|, half-spectrum weight 2 for m > 0, k = 0 and the
 // Nyquist row excluded; optional per-CTA bins of width dk = 2 pi / (ny dx).
+// Partials per CTA (kSfMoments): sum S, sum k S, sum S/k, and for the tensor
+// of Eq. L_matrix sum q_cx^2 S, sum q_cx q_cy S, sum q_cy^2 S, sum S with
+// k = 0 included.
 template <class T>
 __global__ void __launch_bounds__(512) k_sf_cols(const cplx<T>* __restrict__ xs, int log2nx, int log2ny,
                                                   double dx, double s, const cplx<T>* __restrict__ tw,
@@ -125,7 +128,7 @@ __global__ void __launch_bounds__(512) k_sf_cols(const cplx<T>* __restrict__ xs,
                                                   double* __restrict__ bin_partials) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double sh[2 * 3 * 32];
+  __shared__ double sh[2 * kSfMoments * 32];
   const int nx = 1 << log2nx, ny = 1 << log2ny, half = nx >> 1;
   const int Tc = ny >> 3;
   const int col = threadIdx.x / Tc, tid = threadIdx.x - col * Tc;
@@ -146,35 +149,42 @@ __global__ void __launch_bounds__(512) k_sf_cols(const cplx<T>* __restrict__ xs,
   const double qx = two_pi * m / (nx * dx);
   const double norm = 1.0 / ((double)nx * (double)ny);
   const double dk = two_pi / (ny * dx);
-  double acc_s[3] = {0, 0, 0}, acc_c[3] = {0, 0, 0};
+  double acc_s[kSfMoments], acc_c[kSfMoments];
+  for (int v = 0; v < kSfMoments; ++v) acc_s[v] = acc_c[v] = 0.0;
   for (int q = 0; q < 8; ++q) {
     const int n = tid + q * Tc;
     const int idx = col * ny + n;
     double w = 0.0;
     int b = -1;
-    if (n != (ny >> 1) && !(m == 0 && n == 0)) {
+    if (n != (ny >> 1)) {
       const int ns = n < (ny >> 1) ? n : n - ny;
       const double qy = two_pi * ns / (ny * dx);
       const double ky = qy - s * qx;
-      const double k = sqrt(qx * qx + ky * ky);
       const C X = sm[idx];
       const double re = (double)X.x * norm, im = (double)X.y * norm;
       const double S = (m == 0 ? 1.0 : 2.0) * (re * re + im * im);
-      neumaier_add(acc_s[0], acc_c[0], S);
-      neumaier_add(acc_s[1], acc_c[1], k * S);
-      neumaier_add(acc_s[2], acc_c[2], S / k);
-      w = S;
-      const double fb = floor(k / dk);
-      b = (fb < (double)nbins) ? (int)fb : -1;
+      neumaier_add(acc_s[3], acc_c[3], qx * qx * S);
+      neumaier_add(acc_s[4], acc_c[4], qx * ky * S);
+      neumaier_add(acc_s[5], acc_c[5], ky * ky * S);
+      neumaier_add(acc_s[6], acc_c[6], S);
+      if (!(m == 0 && n == 0)) {
+        const double k = sqrt(qx * qx + ky * ky);
+        neumaier_add(acc_s[0], acc_c[0], S);
+        neumaier_add(acc_s[1], acc_c[1], k * S);
+        neumaier_add(acc_s[2], acc_c[2], S / k);
+        w = S;
+        const double fb = floor(k / dk);
+        b = (fb < (double)nbins) ? (int)fb : -1;
+      }
     }
     if (nbins > 0) {
       Sw[idx] = w;
       bin[idx] = b;
     }
   }
-  block_reduce_pairs<3>(acc_s, acc_c, sh);
+  block_reduce_pairs<kSfMoments>(acc_s, acc_c, sh);
   if (threadIdx.x == 0) {
-    for (int v = 0; v < 3; ++v) partials[3 * blockIdx.x + v] = acc_s[v] + acc_c[v];
+    for (int v = 0; v < kSfMoments; ++v) partials[kSfMoments * blockIdx.x + v] = acc_s[v] + acc_c[v];
   }
   if (nbins > 0) {
     __syncthreads();

@@ -599,8 +599,10 @@ int get_fields_t(shf_grid* g, double* phi, double* psi, double* omega) {
   return SHF_OK;
 }
 
-template <class T>
-int sf_t(shf_grid* g, double* S_binned, int nbins, double moments[5]) {
+// The spectral pass over phi (row and column transforms of the current
+// state) with the kSfMoments sums of k_sf_cols reduced in fixed order into
+// sums[], and optionally the radial bins.
+int sf_sums(shf_grid* g, double* S_binned, int nbins, double sums[kSfMoments]) {
   shf_grid* o = owner(g);
   Member& m = *member_of(g);
   SizeClass& cl = o->classes[m.cls];
@@ -608,33 +610,38 @@ int sf_t(shf_grid* g, double* S_binned, int nbins, double moments[5]) {
   long long K;
   host_strain(o->n, m.gdot, m.dt, m.nx / m.ny, &s, &K);
   const ColCfg& cc = cl.sfcols;
-  const size_t need = (size_t)cc.ctas * 3 + 3 + (size_t)cc.ctas * nbins + nbins;
+  const size_t need = (size_t)cc.ctas * kSfMoments + kSfMoments + (size_t)cc.ctas * nbins + nbins;
   int rc = ensure_scratch(o, need);
   if (rc) return fail(g, rc, o->err);
-  rc = ensure_pinned(o, 3 + nbins);
+  rc = ensure_pinned(o, kSfMoments + nbins);
   if (rc) return fail(g, rc, o->err);
   double* parts = o->d_scratch;
-  double* red = parts + (size_t)cc.ctas * 3;
-  double* bparts = red + 3;
+  double* red = parts + (size_t)cc.ctas * kSfMoments;
+  double* bparts = red + kSfMoments;
   double* bred = bparts + (size_t)cc.ctas * nbins;
-  const cplx<T>* tw = static_cast<const cplx<T>*>(o->d_tw);
-  cplx<T>* xs = static_cast<cplx<T>*>(m.xs[1]);
-  launch_sf_rows<T>(static_cast<const T*>(m.phi), xs, cl.log2nx, cl.log2ny, tw, cl.sfrows, o->stream);
-  launch_sf_cols<T>(xs, cl.log2nx, cl.log2ny, m.dx, s, tw, cc, parts, nbins, bparts, o->stream);
-  launch_reduce_rows(parts, cc.ctas, 3, red, o->stream);
+  if (o->precision == SHF_FP64) {
+    using T = double;
+    const cplx<T>* tw = static_cast<const cplx<T>*>(o->d_tw);
+    cplx<T>* xs = static_cast<cplx<T>*>(m.xs[1]);
+    launch_sf_rows<T>(static_cast<const T*>(m.phi), xs, cl.log2nx, cl.log2ny, tw, cl.sfrows, o->stream);
+    launch_sf_cols<T>(xs, cl.log2nx, cl.log2ny, m.dx, s, tw, cc, parts, nbins, bparts, o->stream);
+  } else {
+    using T = float;
+    const cplx<T>* tw = static_cast<const cplx<T>*>(o->d_tw);
+    cplx<T>* xs = static_cast<cplx<T>*>(m.xs[1]);
+    launch_sf_rows<T>(static_cast<const T*>(m.phi), xs, cl.log2nx, cl.log2ny, tw, cl.sfrows, o->stream);
+    launch_sf_cols<T>(xs, cl.log2nx, cl.log2ny, m.dx, s, tw, cc, parts, nbins, bparts, o->stream);
+  }
+  launch_reduce_rows(parts, cc.ctas, kSfMoments, red, o->stream);
   if (nbins > 0) launch_reduce_rows(bparts, cc.ctas, nbins, bred, o->stream);
   SHF_CUDA(g, cudaGetLastError());
-  SHF_CUDA(g, cudaMemcpyAsync(o->h_pinned, red, 3 * sizeof(double), cudaMemcpyDeviceToHost, o->stream));
+  SHF_CUDA(g, cudaMemcpyAsync(o->h_pinned, red, kSfMoments * sizeof(double), cudaMemcpyDeviceToHost, o->stream));
   if (nbins > 0)
-    SHF_CUDA(g, cudaMemcpyAsync(o->h_pinned + 3, bred, nbins * sizeof(double), cudaMemcpyDeviceToHost, o->stream));
+    SHF_CUDA(g, cudaMemcpyAsync(o->h_pinned + kSfMoments, bred, nbins * sizeof(double), cudaMemcpyDeviceToHost,
+                                o->stream));
   SHF_CUDA(g, cudaStreamSynchronize(o->stream));
-  const double S0 = o->h_pinned[0], S1 = o->h_pinned[1], Sm1 = o->h_pinned[2];
-  moments[0] = S0;
-  moments[1] = S1;
-  moments[2] = Sm1;
-  moments[3] = S1 > 0 ? 6.283185307179586476925286766559 * S0 / S1 : NAN;
-  moments[4] = S0 > 0 ? Sm1 / S0 : NAN;
-  if (S_binned && nbins > 0) std::memcpy(S_binned, o->h_pinned + 3, nbins * sizeof(double));
+  for (int v = 0; v < kSfMoments; ++v) sums[v] = o->h_pinned[v];
+  if (S_binned && nbins > 0) std::memcpy(S_binned, o->h_pinned + kSfMoments, nbins * sizeof(double));
   return SHF_OK;
 }
 
@@ -1011,8 +1018,43 @@ int shf_structure_factor(shf_grid* g, double* S_binned, int nbins, double moment
     return fail(g, SHF_EINVAL, "bad structure factor arguments");
   if (g->kind == 1) return fail(g, SHF_EINVAL, "use a member view for an ensemble member");
   SHF_CUDA(g, cudaSetDevice(owner(g)->device));
-  return g->precision == SHF_FP64 ? sf_t<double>(g, S_binned, nbins, moments)
-                                  : sf_t<float>(g, S_binned, nbins, moments);
+  double sums[kSfMoments];
+  const int rc = sf_sums(g, S_binned, nbins, sums);
+  if (rc) return rc;
+  const double S0 = sums[0], S1 = sums[1], Sm1 = sums[2];
+  moments[0] = S0;
+  moments[1] = S1;
+  moments[2] = Sm1;
+  moments[3] = S1 > 0 ? 6.283185307179586476925286766559 * S0 / S1 : NAN;
+  moments[4] = S0 > 0 ? Sm1 / S0 : NAN;
+  return SHF_OK;
+}
+
+int shf_gradient_tensor(shf_grid* g, double G[3], double lengths[2]) {
+  if (!g || !G) return fail(g, SHF_EINVAL, "bad gradient tensor arguments");
+  if (g->kind == 1) return fail(g, SHF_EINVAL, "use a member view for an ensemble member");
+  SHF_CUDA(g, cudaSetDevice(owner(g)->device));
+  double sums[kSfMoments];
+  const int rc = sf_sums(g, nullptr, 0, sums);
+  if (rc) return rc;
+  const double den = sums[6];
+  if (!(den > 0)) {
+    G[0] = G[1] = G[2] = NAN;
+    if (lengths) lengths[0] = lengths[1] = NAN;
+    return fail(g, SHF_ESTATE, "phi is zero: the tensor is undefined");
+  }
+  G[0] = sums[3] / den;
+  G[1] = sums[4] / den;
+  G[2] = sums[5] / den;
+  if (lengths) {
+    const Member& m = *member_of(g);
+    const double ell = std::sqrt(m.kappa / m.a);
+    const double half_tr = 0.5 * (G[0] + G[2]), rad = std::hypot(0.5 * (G[0] - G[2]), G[1]);
+    const double lam_min = half_tr - rad, lam_max = half_tr + rad;
+    lengths[0] = lam_min > 0 ? 1.0 / (ell * lam_min) : INFINITY;
+    lengths[1] = lam_max > 0 ? 1.0 / (ell * lam_max) : INFINITY;
+  }
+  return SHF_OK;
 }
 
 int shf_save(shf_grid* g, const char* path) {

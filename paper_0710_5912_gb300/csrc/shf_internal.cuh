@@ -139,7 +139,9 @@ template <class T> void launch_convert_out(const T* src, double* dst, long long 
 template <class T> int launch_mass_partials(const T* f, long long count, double* out, int max_ctas,
                                             cudaStream_t st);
 // structure factor: row transform of phi into xs (complex ny x nx/2), then per
-// CTA partial moments (sum S, sum kS, sum S/k) and per-CTA bins
+// partial sums per CTA of the structure-factor pass (see k_sf_cols)
+constexpr int kSfMoments = 7;
+// CTA partial moments (kSfMoments per CTA) and per-CTA bins
 template <class T> void launch_sf_rows(const T* phi, cplx<T>* xs, int log2nx, int log2ny,
                                        const cplx<T>* tw, const RowCfg& c, cudaStream_t st);
 template <class T> void launch_sf_cols(const cplx<T>* xs, int log2nx, int log2ny, double dx, double s,

@@ -364,6 +364,51 @@ def test_structure_factor_single_mode_closed_form():
     assert math.isclose(moments[4], 1 / k, rel_tol=1e-13)
 
 
+@pytest.mark.parametrize("prec,tol", [(FP64, 1e-12), (FP32, 2e-6)])
+@pytest.mark.parametrize("shape,gdot", [((128, 64), 0.07), ((64, 64), -0.2), ((256, 128), 0.0)])
+def test_gradient_tensor_matches_oracle(prec, tol, shape, gdot):
+    """Eq. L_matrix on a stepped state (strain nonzero, and past a wrap for the
+    first shape) against the oracle on the same phi."""
+    nx, ny = shape
+    p = oracle.Params(rho=1.0, gdot=gdot, dt=0.01)
+    fields = inputs.quench_state(nx, ny, 4, 0.3)
+    with shf.Grid(nx, ny, 1.0, prec) as g:
+        g.set_params(p.a, p.b, p.kappa, p.M, p.eta, p.rho, p.gdot, p.dt)
+        g.set_fields(*fields)
+        g.step(60)
+        G, L = g.gradient_tensor()
+        phi = g.get_fields()[0]
+        _, _, s, _ = g.get_time()
+    want = oracle.gradient_tensor(phi, s, 1.0)
+    scale = max(abs(want[0]), abs(want[2]))
+    for a, b in zip(G, want):
+        assert abs(a - b) <= tol * scale, (G, want)
+    wl = oracle.principal_lengths(want, math.sqrt(p.kappa / p.a))
+    for a, b in zip(L, wl):
+        assert math.isclose(a, b, rel_tol=10 * tol), (L, wl)
+
+
+def test_gradient_tensor_two_modes_closed_form():
+    nx, ny, s_gdot = 64, 32, 0.3
+    A, B, c = 0.5, 0.2, 0.1
+    phi = (c + inputs.cosine_mode(nx, ny, 2, 1, amp=A) + inputs.cosine_mode(nx, ny, -1, 3, amp=B, phase=0.4))
+    with shf.Grid(nx, ny, 1.0, FP64) as g:
+        g.set_params(kappa=2.0, gdot=s_gdot, dt=0.01)
+        g.set_fields(phi)
+        g.set_step(37)
+        _, _, s, _ = g.get_time()
+        G, L = g.gradient_tensor()
+    num = np.zeros((2, 2))
+    for m, n, a in ((2, 1, A), (-1, 3, B)):
+        qx, qy = 2 * math.pi * m / nx, 2 * math.pi * n / ny
+        q = np.array([qx, qy - s * qx])
+        num += a * a / 2 * np.outer(q, q)
+    want = num / (c * c + (A * A + B * B) / 2)
+    assert np.allclose(G, [want[0, 0], want[0, 1], want[1, 1]], rtol=1e-13, atol=1e-15)
+    ev = np.linalg.eigvalsh(want)
+    assert np.allclose(L, [1 / (math.sqrt(2.0) * ev[0]), 1 / (math.sqrt(2.0) * ev[1])], rtol=1e-12)
+
+
 # --------------------------------------------------------------- error paths
 
 def test_error_paths():
