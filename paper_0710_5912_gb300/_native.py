@@ -21,8 +21,8 @@ BUILD_DIR = os.path.join(PKG_DIR, "_build")
 LIB_DIR = os.path.join(PKG_DIR, "lib")
 LIB_PATH = os.path.join(LIB_DIR, "libshf.so")
 
-SOURCES = ["step_kernels.cu", "diag_kernels.cu", "shf_api.cu", "mass_static.cu"]
-HEADERS = ["fft_block.cuh", "shf_internal.cuh"]
+SOURCES = ["step_kernels.cu", "step_rows.cu", "step_cols.cu", "diag_kernels.cu", "shf_api.cu", "mass_static.cu"]
+HEADERS = ["fft_block.cuh", "shf_internal.cuh", "step_common.cuh"]
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
               "--expt-relaxed-constexpr"]

@@ -178,7 +178,9 @@ LaunchCfg persistent_cfg(int kind, int nfft, int max_inst, int items, size_t ins
   c.threads = ipc * Tf;
   c.smem = ipc * inst_bytes;
   const int work = (items + ipc - 1) / ipc;
-  const int resident = step_kernel_occupancy<T>(kind, c.threads, c.smem) * sm_count();
+  int log2n = 0;
+  while ((1 << log2n) < nfft) ++log2n;
+  const int resident = step_kernel_occupancy<T>(kind, log2n, c.threads, c.smem) * sm_count();
   int g = (resident + nmem - 1) / nmem;
   if (g > work) g = work;
   c.grid_x = g < 1 ? 1 : g;

@@ -115,7 +115,16 @@ struct LaunchCfg {
 
 template <class T> void launch_step_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int log2ny,
                                            const cplx<T>* tw, const LaunchCfg& c, cudaStream_t st);
-template <class T> int step_kernel_occupancy(int kind, int threads, size_t smem);
+template <class T> int step_kernel_occupancy(int kind, int log2n, int threads, size_t smem);
+// the transform kernels by family (step_rows.cu, step_cols.cu)
+template <class T> void launch_row_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int log2ny,
+                                          const cplx<T>* tw, const LaunchCfg& c, cudaStream_t st);
+template <class T> void launch_col_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int log2ny,
+                                          const cplx<T>* tw, const LaunchCfg& c, cudaStream_t st);
+template <class T> int row_kernel_occupancy(int kind, int log2nx, int threads, size_t smem);
+template <class T> int col_kernel_occupancy(int log2ny, int threads, size_t smem);
+template <class T> void set_row_smem_limits(int lim);
+template <class T> void set_col_smem_limits(int lim);
 
 // ---- kernel launchers (step_kernels.cu / diag_kernels.cu) ----
 struct RowCfg {

@@ -1,0 +1,151 @@
+// Device helpers shared by the step kernels (step_kernels.cu: stencils and
+// dispatch; step_rows.cu: row transforms; step_cols.cu: column passes).
+#pragma once
+#include <type_traits>
+
+#include "shf_internal.cuh"
+
+namespace shf {
+
+// minimum resident CTAs per SM requested from the compiler (caps registers)
+template <class T> constexpr int min_ctas() { return sizeof(T) == 8 ? 1 : 2; }
+
+template <class T> struct Layout;
+template <> struct Layout<float> { static constexpr int LC = 1; };   // 2 complex floats = 16 B
+template <> struct Layout<double> { static constexpr int LC = 0; };  // 1 complex double = 16 B
+
+// cells by which row j moves at a wrap: ((K1 - K0) r j) mod nx
+__device__ __forceinline__ int remap_shift(long long dK, int r, int j, int nx) {
+  long long v = ((dK * r) % nx) * j % nx;
+  if (v < 0) v += nx;
+  return (int)v;
+}
+
+// x-spectral element (j, m) in the tiled layout
+__device__ __forceinline__ size_t xs_idx(int j, int m, int ny, int LC) {
+  return ((((size_t)(m >> LC) * ny) + j) << LC) | (size_t)(m & ((1 << LC) - 1));
+}
+
+// Strain s, wrap flag and the weights of the sheared y-derivative (Eq. p1y):
+// D_y^s f = [w0 (f(i, j+1) - f(i, j-1)) + w1 (f(i+d, j+1) - f(i-d, j-1))] / 2h,
+// w1 = |s|/2, w0 = 1 - w1, d = -2 for s >= 0 and +2 for s < 0.
+template <class T>
+struct Shear {
+  T s, w0, w1;
+  int d;
+  long long dK;   // K(n+1) - K(n): nonzero when the strain wraps during the step
+  // next = false: s = s(t^n) (stage 1); next = true: s = s(t^{n+1}) (stages 2-3)
+  __device__ __forceinline__ Shear(const StepState& S, bool next) {
+    s = (T)(next ? S.s1 : S.s0);
+    w1 = (s < T(0) ? -s : s) * T(0.5);
+    w0 = T(1) - w1;
+    d = s >= T(0) ? -2 : 2;
+    dK = S.dK;
+  }
+};
+
+// one thread: the StepState of member D for the step starting at n
+__device__ __forceinline__ void step_state_set(const MemberDesc& D, long long n) {
+  double s0, s1;
+  long long K0, K1;
+  strain_dev(n, D.gdot, D.dt, D.ratio, s0, K0);
+  strain_dev(n + 1, D.gdot, D.dt, D.ratio, s1, K1);
+  StepState* S = D.st;
+  S->n = n;
+  S->dK = K1 - K0;
+  S->s0 = s0;
+  S->s1 = s1;
+}
+
+
+// ---- asynchronous global -> shared copies (cp.async; the wait is a hardware
+// instruction, not a spin loop)
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async16(void* s, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* s, const void* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// bytes (a multiple of 16, both ends 16-byte aligned) from src to dst
+__device__ __forceinline__ void copy_async(void* dst, const void* src, int bytes, int t, int nthr) {
+  char* d = static_cast<char*>(dst);
+  const char* s = static_cast<const char*>(src);
+  for (int off = t * 16; off < bytes; off += nthr * 16) cp_async16(d + off, s + off);
+}
+
+// Half spectra of two real rows a, b from Z = FFT(a + i b) held in a padded
+// buffer: A[m] = (Z[m] + conj Z[N-m]) / 2, B[m] = (Z[m] - conj Z[N-m]) / (2i).
+template <class C>
+__device__ __forceinline__ void split_pair(const C* z, int m, int mx, C& A, C& B) {
+  using T = decltype(z[0].x);
+  const C zk = z[pad16(m)];
+  const C zc = cconj(z[pad16((-m) & mx)]);
+  A = C{(zk.x + zc.x) * T(0.5), (zk.y + zc.y) * T(0.5)};
+  B = C{(zk.y - zc.y) * T(0.5), -(zk.x - zc.x) * T(0.5)};
+}
+
+// Z holds FFT(row j0 + i row j0+1) of one field: both half spectra -> dst.
+// A thread writes whole chunks of the pair: 2 CL elements = 32 contiguous
+// bytes (a full sector), as two 16-byte stores in FP32.
+template <int LC, class C>
+__device__ __forceinline__ void write_pair_rows(const C* z, C* dst, int j0, int nx, int ny, int t, int Tthreads) {
+  constexpr int CL = 1 << LC;
+  const int mx = nx - 1;
+  const int nchunk = (nx >> 1) >> LC;
+  for (int cb = t; cb < nchunk; cb += Tthreads) {
+    C* p = dst + ((((size_t)cb * ny) + j0) << LC);
+    C A[CL], B[CL];
+#pragma unroll
+    for (int c = 0; c < CL; ++c) split_pair(z, (cb << LC) + c, mx, A[c], B[c]);
+    if constexpr (CL == 2) {
+      reinterpret_cast<float4*>(p)[0] = make_float4(A[0].x, A[0].y, A[1].x, A[1].y);
+      reinterpret_cast<float4*>(p)[1] = make_float4(B[0].x, B[0].y, B[1].x, B[1].y);
+    } else {
+#pragma unroll
+      for (int c = 0; c < CL; ++c) {
+        p[c] = A[c];
+        p[CL + c] = B[c];
+      }
+    }
+  }
+}
+
+// v[q] = Z[t + T q] from a padded buffer (the register layout of fft_reg)
+template <class C>
+__device__ __forceinline__ void smem_to_reg(C (&v)[kP], const C* Z, int log2N, int t) {
+  const int T = 1 << (log2N - kLogP);
+#pragma unroll
+  for (int q = 0; q < kP; ++q) v[q] = Z[pad16(t + q * T)];
+}
+
+// Number of loop iterations of a persistent CTA: every instance of the CTA runs
+// the same count (the loop body has barriers); an instance whose item is past
+// the end idles through its last iteration.
+__device__ __forceinline__ int persistent_iters(int nitems, int ipc) {
+  const int stride = gridDim.x * ipc;
+  const int first = blockIdx.x * ipc;
+  return first < nitems ? (nitems - first + stride - 1) / stride : 0;
+}
+
+// Calls f(std::integral_constant<int, L>{}) for L = ln, the log2 of a transform
+// length in [4, LOG2_NMAX]: the transform kernels are compiled per length.
+template <class F>
+inline void with_log2n(int ln, F&& f) {
+  switch (ln) {
+    case 4: f(std::integral_constant<int, 4>{}); break;
+    case 5: f(std::integral_constant<int, 5>{}); break;
+    case 6: f(std::integral_constant<int, 6>{}); break;
+    case 7: f(std::integral_constant<int, 7>{}); break;
+    case 8: f(std::integral_constant<int, 8>{}); break;
+    case 9: f(std::integral_constant<int, 9>{}); break;
+    case 10: f(std::integral_constant<int, 10>{}); break;
+    case 11: f(std::integral_constant<int, 11>{}); break;
+    default: f(std::integral_constant<int, 12>{}); break;
+  }
+}
+
+}  // namespace shf

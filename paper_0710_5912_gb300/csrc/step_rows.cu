@@ -1,0 +1,265 @@
+// Row (x) transforms of a step: k_rowfwd (rowfwd_phi, rowfwd_g) and k_rowinv
+// (rowinv_phi, rowinv_flow), compiled per row length nx = 2^LN.  See
+// step_kernels.cu for the step's kernels and the x-spectral layout.
+#include "step_common.cuh"
+
+namespace shf {
+
+// ====================================================== forward row transforms
+// Work items: mode 0 (phi): per row pair p = rows (2p, 2p+1), item 0 = phi*,
+// item 1 = f = phi^3, item 2 = omega* (inertial members); mode 1 (g): one item
+// per row pair.  Each item stages the two real rows (a, b) in shared memory and
+// transforms a + i b (for f the staged phi rows are cubed on the fly), so every
+// output chunk of the pair is one whole 32-byte piece.
+template <class T, int LN>
+__global__ void __launch_bounds__(512, min_ctas<T>()) k_rowfwd(const MemberDesc* __restrict__ descs, int log2ny,
+                                                               const cplx<T>* __restrict__ tw, int mode) {
+  constexpr int log2nx = LN;
+  using C = cplx<T>;
+  constexpr int LC = Layout<T>::LC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const MemberDesc& D = descs[blockIdx.y];
+  const int nx = 1 << log2nx, ny = 1 << log2ny;
+  const int Tf = nx >> kLogP;
+  const int ipc = blockDim.x / Tf;
+  const int inst = threadIdx.x / Tf, t = threadIdx.x - inst * Tf;
+  const int nsub = mode == 0 ? (D.stokes ? 2 : 3) : 1;
+  const int nitems = (ny >> 1) * nsub;
+  const int stride = gridDim.x * ipc;
+  unsigned char* base = smem_raw + (size_t)inst * rowfwd_inst_bytes(nx, sizeof(T));
+  T* stage = reinterpret_cast<T*>(base);
+  C* Z = reinterpret_cast<C*>(base + 2 * (size_t)nx * sizeof(T));
+  const T* phis = static_cast<const T*>(D.phi_star);
+  const T* phi = static_cast<const T*>(D.phi);
+  const T* oms = static_cast<const T*>(D.omega_star);
+  const T* gb = static_cast<const T*>(D.gbuf);
+
+  auto issue = [&](int w) {
+    if (w < nitems) {
+      const int p = w / nsub, sub = w - p * nsub;
+      const T *ra, *rb;
+      if (mode == 1) {
+        ra = gb + ((size_t)(2 * p) << log2nx);
+        rb = gb + ((size_t)(2 * p + 1) << log2nx);
+      } else if (sub < 2) {
+        const T* src = sub == 0 ? phis : phi;             // phi* pair, or phi pair (cubed on the fly)
+        ra = src + ((size_t)(2 * p) << log2nx);
+        rb = src + ((size_t)(2 * p + 1) << log2nx);
+      } else {
+        ra = oms + ((size_t)(2 * p) << log2nx);
+        rb = oms + ((size_t)(2 * p + 1) << log2nx);
+      }
+      copy_async(stage, ra, nx * (int)sizeof(T), t, Tf);
+      copy_async(stage + nx, rb, nx * (int)sizeof(T), t, Tf);
+    }
+    cp_async_commit();
+  };
+
+  const int iters = persistent_iters(nitems, ipc);
+  int w = blockIdx.x * ipc + inst;
+  issue(w);
+  for (int it = 0; it < iters; ++it, w += stride) {
+    const bool active = w < nitems;
+    const int p = w / nsub, sub = w - p * nsub;
+    const bool cube = mode == 0 && sub == 1;
+    cp_async_wait_all();
+    __syncthreads();
+    C v[kP];
+#pragma unroll
+    for (int q = 0; q < kP; ++q) {
+      const int i = t + q * Tf;
+      const T a = stage[i], bb = stage[nx + i];
+      v[q] = cube ? C{(a * a) * a, (bb * bb) * bb} : C{a, bb};
+    }
+    __syncthreads();                                    // stage free
+    issue(w + stride);                                  // next item streams in during the transform
+    fft_reg<false>(v, log2nx, t, Z, tw);
+    reg_to_smem(v, log2nx, t, Z);
+    if (active) {
+      if (mode == 1) {
+        write_pair_rows<LC>(Z, static_cast<C*>(D.xs_g), 2 * p, nx, ny, t, Tf);
+      } else if (sub < 2) {
+        write_pair_rows<LC>(Z, static_cast<C*>(sub == 0 ? D.xs_phi : D.xs_f), 2 * p, nx, ny, t, Tf);
+        if (sub == 0 && t == 0) {                        // phi*'s row Nyquist coefficients
+          const C zn = Z[pad16(nx >> 1)];
+          static_cast<T*>(D.nyq_phi)[2 * p] = zn.x;
+          static_cast<T*>(D.nyq_phi)[2 * p + 1] = zn.y;
+        }
+      } else {
+        write_pair_rows<LC>(Z, static_cast<C*>(D.xs_w), 2 * p, nx, ny, t, Tf);
+        if (t == 0) {
+          const C zn = Z[pad16(nx >> 1)];
+          static_cast<T*>(D.nyq_omega)[2 * p] = zn.x;
+          static_cast<T*>(D.nyq_omega)[2 * p + 1] = zn.y;
+        }
+      }
+    }
+    __syncthreads();                                    // Z reads done before the next transform
+  }
+  cp_async_wait_all();
+}
+
+// ====================================================== inverse row transforms
+// Work items: mode 0 (phi): row pairs of the phi increment; mode 1 (flow): per
+// row pair, item 0 = psi, item 1 = the omega increment (inertial members).  The
+// item's 32-byte chunks stream into the staging buffer during the previous
+// transform; Z[k] = A[k] + i B[k], Z[N-k] = conj A[k] + i conj B[k] (A, B the
+// two rows), Z[0] from the real parts, Z[N/2] = minus the staged field's row
+// Nyquist coefficients / nx.
+template <class T, int LN>
+__global__ void __launch_bounds__(512, min_ctas<T>()) k_rowinv(const MemberDesc* __restrict__ descs, int log2ny,
+                                                               const cplx<T>* __restrict__ tw, int mode) {
+  constexpr int log2nx = LN;
+  using C = cplx<T>;
+  constexpr int LC = Layout<T>::LC;
+  constexpr int CL = 1 << LC;
+  constexpr int H = 16 / sizeof(C);                     // complex values per 16 bytes
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const MemberDesc& D = descs[blockIdx.y];
+  const int nx = 1 << log2nx, ny = 1 << log2ny, mx = nx - 1;
+  const int Tf = nx >> kLogP;
+  const int ipc = blockDim.x / Tf;
+  const int inst = threadIdx.x / Tf, t = threadIdx.x - inst * Tf;
+  const int nsub = (mode == 1 && !D.stokes) ? 2 : 1;
+  const int nitems = (ny >> 1) * nsub;
+  const int stride = gridDim.x * ipc;
+  const int nchunk = (nx >> 1) >> LC;
+  unsigned char* base = smem_raw + (size_t)inst * rowinv_inst_bytes(nx, sizeof(T));
+  C* stage = reinterpret_cast<C*>(base);               // chunk cb at stage[2 CL cb]
+  C* Z = stage + nx;
+
+  auto issue = [&](int w) {
+    if (w < nitems) {
+      const int sub = w % nsub;
+      const C* src = static_cast<const C*>(mode == 0 ? D.xs_phi : (sub == 0 ? D.xs_g : D.xs_w));
+      const int j0 = 2 * (w / nsub);
+      for (int cb = t; cb < nchunk; cb += Tf) {
+        const C* g = src + ((((size_t)cb * ny) + j0) << LC);
+        cp_async16(stage + 2 * CL * cb, g);
+        cp_async16(stage + 2 * CL * cb + H, g + H);
+      }
+    }
+    cp_async_commit();
+  };
+
+  const long long dK = (mode == 0 && D.remap) ? D.st->dK : 0;
+  const T rn = T(1) / T(nx);
+  const int iters = persistent_iters(nitems, ipc);
+  int w = blockIdx.x * ipc + inst;
+  issue(w);
+  for (int it = 0; it < iters; ++it, w += stride) {
+    const bool active = w < nitems;
+    const int p = w / nsub, sub = w - p * nsub;
+    const int j0 = 2 * p, j1 = j0 + 1;
+    const int kind = mode == 0 ? 0 : (sub == 0 ? 1 : 2);   // phi increment, psi, omega increment
+    C zn = C{T(0), T(0)};
+    if (active && kind != 1) {
+      const T* nq = static_cast<const T*>(kind == 0 ? D.nyq_phi : D.nyq_omega);
+      zn = C{-nq[j0] * rn, -nq[j1] * rn};
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int cb = t; cb < nchunk; cb += Tf) {
+#pragma unroll
+      for (int c = 0; c < CL; ++c) {
+        const int k = (cb << LC) + c;
+        const C A = stage[2 * CL * cb + c], B = stage[2 * CL * cb + CL + c];
+        if (k == 0) {
+          Z[pad16(0)] = C{A.x, B.x};
+          Z[pad16(nx >> 1)] = zn;
+        } else {
+          Z[pad16(k)] = C{A.x - B.y, A.y + B.x};
+          Z[pad16(nx - k)] = C{A.x + B.y, B.x - A.y};
+        }
+      }
+    }
+    __syncthreads();                                    // Z complete, stage free
+    issue(w + stride);
+    C v[kP];
+    smem_to_reg(v, Z, log2nx, t);
+    __syncthreads();                                    // Z becomes the exchange buffer
+    // the real-space base of the increment (phi* or omega*), loaded before the transform
+    T b0[kP], b1[kP];
+    if (active && kind != 1) {
+      const T* bs = static_cast<const T*>(kind == 0 ? D.phi_star : D.omega_star);
+#pragma unroll
+      for (int q = 0; q < kP; ++q) {
+        b0[q] = bs[((size_t)j0 << log2nx) + t + q * Tf];
+        b1[q] = bs[((size_t)j1 << log2nx) + t + q * Tf];
+      }
+    }
+    fft_reg<true>(v, log2nx, t, Z, tw);
+    if (active) {
+      if (kind == 1) {
+        T* out = static_cast<T*>(D.psi);
+#pragma unroll
+        for (int q = 0; q < kP; ++q) {
+          out[((size_t)j0 << log2nx) + t + q * Tf] = v[q].x;
+          out[((size_t)j1 << log2nx) + t + q * Tf] = v[q].y;
+        }
+      } else {
+        T* out = static_cast<T*>(kind == 0 ? D.phi : D.omega);
+        const int sh0 = (kind == 0 && dK) ? remap_shift(dK, D.ratio, j0, nx) : 0;
+        const int sh1 = (kind == 0 && dK) ? remap_shift(dK, D.ratio, j1, nx) : 0;
+#pragma unroll
+        for (int q = 0; q < kP; ++q) {
+          const int i = t + q * Tf;
+          out[((size_t)j0 << log2nx) + ((i + sh0) & mx)] = b0[q] + v[q].x;
+          out[((size_t)j1 << log2nx) + ((i + sh1) & mx)] = b1[q] + v[q].y;
+        }
+      }
+    }
+  }
+  cp_async_wait_all();
+  // the next step's state; no CTA of this launch reads it
+  if (mode == 1 && blockIdx.x == 0 && threadIdx.x == 0) step_state_set(D, D.st->n + 1);
+}
+
+// ----------------------------------------------------------------- launchers
+template <class T>
+void launch_row_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int log2ny, const cplx<T>* tw,
+                       const LaunchCfg& c, cudaStream_t st) {
+  const dim3 grid(c.grid_x, nmem);
+  with_log2n(log2nx, [&](auto L) {
+    constexpr int LN = decltype(L)::value;
+    switch (kind) {
+      case KIND_ROWFWD_PHI: k_rowfwd<T, LN><<<grid, c.threads, c.smem, st>>>(d, log2ny, tw, 0); break;
+      case KIND_ROWFWD_G: k_rowfwd<T, LN><<<grid, c.threads, c.smem, st>>>(d, log2ny, tw, 1); break;
+      case KIND_ROWINV_PHI: k_rowinv<T, LN><<<grid, c.threads, c.smem, st>>>(d, log2ny, tw, 0); break;
+      default: k_rowinv<T, LN><<<grid, c.threads, c.smem, st>>>(d, log2ny, tw, 1); break;
+    }
+  });
+}
+
+template <class T>
+int row_kernel_occupancy(int kind, int log2nx, int threads, size_t smem) {
+  int nb = 0;
+  with_log2n(log2nx, [&](auto L) {
+    constexpr int LN = decltype(L)::value;
+    const void* f = (kind == KIND_ROWFWD_PHI || kind == KIND_ROWFWD_G) ? (const void*)k_rowfwd<T, LN>
+                                                                        : (const void*)k_rowinv<T, LN>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads, smem) != cudaSuccess) nb = 1;
+  });
+  return nb < 1 ? 1 : nb;
+}
+
+template <class T>
+void set_row_smem_limits(int lim) {
+  for (int ln = 4; ln <= LOG2_NMAX; ++ln)
+    with_log2n(ln, [&](auto L) {
+      constexpr int LN = decltype(L)::value;
+      cudaFuncSetAttribute(k_rowfwd<T, LN>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      cudaFuncSetAttribute(k_rowinv<T, LN>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    });
+}
+
+#define SHF_ROW_INST(T)                                                                                   \
+  template void launch_row_kernel<T>(int, const MemberDesc*, int, int, int, const cplx<T>*, const LaunchCfg&, \
+                                     cudaStream_t);                                                        \
+  template int row_kernel_occupancy<T>(int, int, int, size_t);                                             \
+  template void set_row_smem_limits<T>(int);
+
+SHF_ROW_INST(float)
+SHF_ROW_INST(double)
+
+}  // namespace shf
