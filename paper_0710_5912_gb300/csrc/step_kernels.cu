@@ -117,6 +117,26 @@ __device__ __forceinline__ Row8<T> ld8(const T* p) {
   return Row8<T>{{a.v[0], a.v[1], a.v[2], a.v[3], b.v[0], b.v[1], b.v[2], b.v[3]}};
 }
 
+// Six reals of a tile row, cols c - 1 .. c + 4 (c a multiple of 4), read as
+// pairs at c - 2 and c + 4 and a quad at c: the stencil row of a 4-point
+// block of second differences whose first point sits at c.
+template <class T>
+struct Six {
+  T v[6];
+};
+__device__ __forceinline__ Six<float> ld6(const float* p) {
+  const float2 l = *reinterpret_cast<const float2*>(p - 2);
+  const float4 m = *reinterpret_cast<const float4*>(p);
+  const float2 r = *reinterpret_cast<const float2*>(p + 4);
+  return Six<float>{{l.y, m.x, m.y, m.z, m.w, r.x}};
+}
+__device__ __forceinline__ Six<double> ld6(const double* p) {
+  const double2 l = *reinterpret_cast<const double2*>(p - 2);
+  const double2 m0 = reinterpret_cast<const double2*>(p)[0], m1 = reinterpret_cast<const double2*>(p)[1];
+  const double2 r = *reinterpret_cast<const double2*>(p + 4);
+  return Six<double>{{l.y, m0.x, m0.y, m1.x, m1.y, r.x}};
+}
+
 // Derivatives at the 4 points (centre index p + 2) of rows U (j+1), C (j),
 // Dn (j-1): D_x f = (f(i+1) - f(i-1)) / 2h and Eq. p1y's sheared D_y^s f =
 // [w0 (f(i, j+1) - f(i, j-1)) + w1 (f(i+d, j+1) - f(i-d, j-1))] / 2h, with
@@ -134,8 +154,16 @@ __device__ __forceinline__ void grad4(const Row8<T>& U, const Row8<T>& C, const 
 }
 
 // Fill rows [0, H) of NF tiles (tile column c <-> x0 - OFF + c, OFF = 2 or 6,
-// width TX + 2 OFF) from NF fields at rows y0 - HY + r (periodic).  Interior
-// quads are 16-byte global loads; the OFF halo columns on each side are pairs.
+// width TX + 2 OFF) from NF fields at rows y0 - HY + r (periodic), with
+// asynchronous copies (all of a thread's copies are in flight at once) of two
+// reals each: the interior in pairs, the OFF halo columns on each side as
+// pairs.  Returns after the copies have landed (this thread's; the caller
+// then synchronises the CTA).
+template <class T>
+__device__ __forceinline__ void cp_async_pair(T* dst, const T* src) {
+  if (sizeof(T) == 4) cp_async8(dst, src);
+  else cp_async16(dst, src);
+}
 template <class T, int TX, int OFF, int H, int NF>
 __device__ __forceinline__ void fill_tiles(T* tile, const T* const* src, int x0, int yb, int log2nx, int my,
                                            int tid, int nthr) {
@@ -149,24 +177,20 @@ __device__ __forceinline__ void fill_tiles(T* tile, const T* const* src, int x0,
     const T* row = src[f] + ((size_t)((yb + r) & my) << log2nx);
     T* trow = tile + ((size_t)f * H + r) * W;
     if (k < QX) {
-      const Quad<T> q = ldg4(row + x0 + 4 * k);
+      const T* g = row + x0 + 4 * k;
       T* d = trow + OFF + 4 * k;
-      if (OFF % 4 == 0) {
-        st4(d, q.v[0], q.v[1], q.v[2], q.v[3]);
-      } else {
-        st2(d, q.v[0], q.v[1]);
-        st2(d + 2, q.v[2], q.v[3]);
-      }
+      cp_async_pair(d, g);
+      cp_async_pair(d + 2, g + 2);
     } else {
       const int h = k - QX;                               // 0 .. 2 HP - 1
       const int side = h / HP, j = h - side * HP;         // left (0) or right (1) halo, pair j
       const int c = side == 0 ? 2 * j : OFF + TX + 2 * j;
       const int x = (x0 - OFF + c) & mx;                  // even, so the pair is contiguous
-      T a, b;
-      ldg2(row + x, a, b);
-      st2(trow + c, a, b);
+      cp_async_pair(trow + c, row + x);
     }
   }
+  cp_async_commit();
+  cp_async_wait_all();
 }
 
 // stage-1 stencil: phi* = phi - dt J(psi, phi), omega* = omega - dt J(psi, omega)
@@ -253,48 +277,60 @@ __device__ __forceinline__ void stencil2_body(const MemberDesc& D, const T* tp, 
   const T a = (T)D.a, b = (T)D.b, kappa = (T)D.kappa;
   const T ih2 = (T)D.inv_h2, i4h2 = (T)D.inv_4h2, inv2h = (T)D.inv_2h;
   const T cxx = T(1) + sc.s * sc.s, cxy = T(2) * sc.s;
-  // mu tile row rm <-> y0 - 1 + rm <-> phi tile row rm + 1; mu quad at tile col 4 (k + 1)
-  for (int e = tid; e < HM * NQ; e += nthr) {
-    const int rm = e / NQ, k = e - rm * NQ;
+  // mu tile row rm <-> y0 - 1 + rm <-> phi tile row rm + 1; mu quad at tile col 4 (k + 1).
+  // Work unit: one quad column k over RPT consecutive mu rows, with a three-row
+  // window of phi (one new phi row per mu row).
+  constexpr int NT = QX * (TY / 4);                    // threads of the CTA
+  constexpr int RG = NT / NQ;                          // row groups
+  constexpr int RPT = (HM + RG - 1) / RG;              // mu rows per unit
+  if (tid < NQ * RG) {
+    const int k = tid % NQ, rg = tid / NQ;
     const int c = 4 * (k + 1);
-    const T* pr = tp + (rm + 1) * W;
-    const Quad<T> Cl = ld4(pr + c - 4), Cc = ld4(pr + c), Cr = ld4(pr + c + 4);
-    const Quad<T> Ul = ld4(pr + W + c - 4), Uc = ld4(pr + W + c), Ur = ld4(pr + W + c + 4);
-    const Quad<T> Dl = ld4(pr - W + c - 4), Dc = ld4(pr - W + c), Dr = ld4(pr - W + c + 4);
-    const T cw[6] = {Cl.v[3], Cc.v[0], Cc.v[1], Cc.v[2], Cc.v[3], Cr.v[0]};
-    const T uw[6] = {Ul.v[3], Uc.v[0], Uc.v[1], Uc.v[2], Uc.v[3], Ur.v[0]};
-    const T dw[6] = {Dl.v[3], Dc.v[0], Dc.v[1], Dc.v[2], Dc.v[3], Dr.v[0]};
-    T m[4];
+    const int r0 = rg * RPT, r1 = min(r0 + RPT, HM);
+    Six<T> Dn = ld6(tp + r0 * W + c), Cn = ld6(tp + (r0 + 1) * W + c);
+    for (int rm = r0; rm < r1; ++rm) {
+      const Six<T> Un = ld6(tp + (rm + 2) * W + c);
+      T m[4];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      const T pc = cw[p + 1];
-      const T dxx = (cw[p + 2] - T(2) * pc + cw[p]) * ih2;
-      const T dyy = (uw[p + 1] - T(2) * pc + dw[p + 1]) * ih2;
-      const T dxy = (uw[p + 2] - dw[p + 2] - uw[p] + dw[p]) * i4h2;
-      const T lap = cxx * dxx - cxy * dxy + dyy;
-      m[p] = -a * pc + b * ((pc * pc) * pc) - kappa * lap;
+      for (int p = 0; p < 4; ++p) {
+        const T pc = Cn.v[p + 1];
+        const T dxx = (Cn.v[p + 2] - T(2) * pc + Cn.v[p]) * ih2;
+        const T dyy = (Un.v[p + 1] - T(2) * pc + Dn.v[p + 1]) * ih2;
+        const T dxy = (Un.v[p + 2] - Dn.v[p + 2] - Un.v[p] + Dn.v[p]) * i4h2;
+        const T lap = cxx * dxx - cxy * dxy + dyy;
+        m[p] = -a * pc + b * ((pc * pc) * pc) - kappa * lap;
+      }
+      st4(tm + rm * W + c, m[0], m[1], m[2], m[3]);
+      Dn = Cn;
+      Cn = Un;
     }
-    st4(tm + rm * W + c, m[0], m[1], m[2], m[3]);
   }
   __syncthreads();
   const int q = tid % QX, g = tid / QX;
   const T cf = (T)D.c_force;
   T* gout = static_cast<T*>(D.gbuf);
   const int x = x0 + 4 * q;
-  // the 8-wide rows of output block (cols x - 2 .. x + 5) start at tile col 4 q + 4
+  // the 8-wide rows of output block (cols x - 2 .. x + 5) start at tile col 4 q + 4;
+  // output row y0 + 4 g + o is phi tile row 4 g + 2 + o and mu tile row 4 g + 1 + o
+  const T* pcol = tp + 4 * q + 4;
+  const T* mcol = tm + 4 * q + 4;
+  Row8<T> pD = ld8(pcol + (4 * g + 1) * W), pC = ld8(pcol + (4 * g + 2) * W);
+  Row8<T> mD = ld8(mcol + (4 * g) * W), mC = ld8(mcol + (4 * g + 1) * W);
 #pragma unroll
   for (int o = 0; o < 4; ++o) {
     const int y = y0 + 4 * g + o;
-    const int rp = 4 * g + 2 + o, rmu = 4 * g + 1 + o;   // phi and mu tile rows of y
+    const Row8<T> pU = ld8(pcol + (4 * g + 3 + o) * W), mU = ld8(mcol + (4 * g + 2 + o) * W);
     T dxp[4], dyp[4], dxm[4], dym[4];
-    grad4<NEG>(ld8(tp + (rp + 1) * W + 4 * q + 4), ld8(tp + rp * W + 4 * q + 4), ld8(tp + (rp - 1) * W + 4 * q + 4),
-               sc.w0, sc.w1, inv2h, dxp, dyp);
-    grad4<NEG>(ld8(tm + (rmu + 1) * W + 4 * q + 4), ld8(tm + rmu * W + 4 * q + 4),
-               ld8(tm + (rmu - 1) * W + 4 * q + 4), sc.w0, sc.w1, inv2h, dxm, dym);
+    grad4<NEG>(pU, pC, pD, sc.w0, sc.w1, inv2h, dxp, dyp);
+    grad4<NEG>(mU, mC, mD, sc.w0, sc.w1, inv2h, dxm, dym);
     T r[4];
 #pragma unroll
     for (int p = 0; p < 4; ++p) r[p] = cf * (dxp[p] * dym[p] - dyp[p] * dxm[p]);
     st4(gout + ((size_t)y << log2nx) + x, r[0], r[1], r[2], r[3]);
+    pD = pC;
+    pC = pU;
+    mD = mC;
+    mC = mU;
   }
 }
 
