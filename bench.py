@@ -51,8 +51,9 @@ KERNEL_REALS_PER_POINT = {
     "colpass_flow": 4,    # g, omega* in; psi, omega increment out
     "rowinv_flow": 5,     # psi, omega increment, omega* in; psi, omega out
 }
-KERNEL_SOURCES = ["paper_0710_5912_gb300/csrc/step_kernels.cu", "paper_0710_5912_gb300/csrc/fft_block.cuh",
-                  "paper_0710_5912_gb300/csrc/shf_internal.cuh"]
+KERNEL_SOURCES = ["paper_0710_5912_gb300/csrc/step_kernels.cu", "paper_0710_5912_gb300/csrc/step_rows.cu",
+                  "paper_0710_5912_gb300/csrc/step_cols.cu", "paper_0710_5912_gb300/csrc/step_common.cuh",
+                  "paper_0710_5912_gb300/csrc/fft_block.cuh", "paper_0710_5912_gb300/csrc/shf_internal.cuh"]
 WORKLOAD = ("4096x4096 inertial model H, FP32 bulk with FP64 strain/phase/mass, rho=eta=1, a=b=kappa=M=1, "
             "dx=1, gdot=0.001, dt=0.005, seeded +-0.01 quench")
 
@@ -101,7 +102,8 @@ def profiled_traffic(kernel):
     vals = {}
     with open(path) as f:
         for line in f:
-            if ":" in line and line.strip().startswith(("dram_bytes_per_launch", "source_sha256")):
+            line = line.strip().lstrip("-").strip()
+            if ":" in line and line.startswith(("dram_bytes_per_launch", "source_sha256")):
                 k, v = line.split(":", 1)
                 vals[k.strip()] = v.strip().strip("`")
     if vals.get("source_sha256") != sources_sha():
