@@ -164,6 +164,24 @@ def test_fp64_200_steps_rect(rho):
     assert_close(got, want, 1e-10, rho, "128x64 fp64")
 
 
+@pytest.mark.parametrize("prec", [FP64, FP32])
+@pytest.mark.parametrize("rho", [0.0, 0.05])
+def test_paper_geometry_1024x512_across_a_wrap(prec, rho):
+    """The paper's sheared geometry Lx = 2 Ly (Table I, 1024 x 512): the remap
+    shifts row j by 2j cells.  gdot dt = 2^-5 puts the wrap at step 32; steps
+    28..36 cross it."""
+    nx, ny = 1024, 512
+    p = oracle.Params(a=1, b=1, kappa=1, M=1, eta=1, rho=rho, gdot=2.0 ** -5 / 0.004, dt=0.004)
+    fields = rough_state(nx, ny, 21, rho > 0)
+    fields = tuple(0.1 * f for f in fields)
+    K0 = oracle.strain(28, p.gdot, p.dt, nx, ny)[1]
+    s_end, K1 = oracle.strain(36, p.gdot, p.dt, nx, ny)
+    assert K1 == K0 + 1
+    got = gpu_run(nx, ny, prec, p, fields, 28, 8)
+    want = oracle_run(p, fields, 28, 8)
+    assert_close(got, want, TOL_1[prec] * 10, rho, f"1024x512 rho={rho}", prec, s_end, 1.0)
+
+
 @pytest.mark.parametrize("rho", [0.0, 0.1, 1.0])
 def test_config_1024_side_by_side(rho):
     """1024x1024 FP32, eta = 1, gdot = 0.003, dt = 0.005: a few steps against the oracle."""

@@ -1,0 +1,65 @@
+"""Regime checks on long GPU runs (smoke tests, not parity): the qualitative
+results the paper reports, on the seeded quench.
+
+- Section VII / III: diffusive coarsening in zero shear follows
+  L ~ t^(1/3) (Eq. LD); with a very large viscosity the flow is negligible and
+  the growth exponent of L_s (Eq. L_structure) comes out near 1/3.
+- Section VIII: without inertia, under shear the long domain axis L_par grows
+  without bound until it spans the system, with the domains aligned along the
+  flow (Eq. L_matrix's principal axes).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import paper_0710_5912_gb300 as shf
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    shf.lib()
+
+
+def test_diffusive_coarsening_exponent_one_third():
+    nx = ny = 256
+    dt = 0.05
+    times = [500, 1000, 2000, 4000, 8000]
+    Ls = []
+    with shf.Grid(nx, ny, 1.0, shf.SHF_FP32) as g:
+        g.set_params(a=1, b=1, kappa=1, M=1, eta=1000.0, rho=0.0, gdot=0.0, dt=dt)
+        g.init_noise(0, 0.01)
+        m0 = g.mass()
+        n = 0
+        for t in times:
+            k = int(round(t / dt)) - n
+            g.step(k)
+            n += k
+            moments, _ = g.structure_factor()
+            Ls.append(moments[4])
+        # the mean of phi is conserved up to FP32 rounding of each step's
+        # increments, a random walk of about eps32 per step
+        assert abs(g.mass() - m0) < 3 * 2.0 ** -24 * math.sqrt(n)
+    slope = np.polyfit(np.log(times), np.log(Ls), 1)[0]
+    assert 0.27 <= slope <= 0.40, (slope, Ls)
+    assert all(b > a for a, b in zip(Ls, Ls[1:]))
+
+
+def test_inertialess_shear_domains_span_the_system_along_the_flow():
+    nx = ny = 256
+    gdot, dt = 0.02, 0.02
+    with shf.Grid(nx, ny, 1.0, shf.SHF_FP32) as g:
+        g.set_params(a=1, b=1, kappa=1, M=1, eta=1.0, rho=0.0, gdot=gdot, dt=dt)
+        g.init_noise(1, 0.01)
+        g.step(int(round(40 / gdot / dt)))                # 40 strain units
+        G, (Lpar, Lperp) = g.gradient_tensor()
+    # the larger-gradient principal axis is close to y: domains lie along x (the flow)
+    angle = 0.5 * math.degrees(math.atan2(2 * G[1], G[0] - G[2]))
+    assert abs(abs(angle) - 90.0) < 20.0, angle
+    assert Lpar > 5 * Lperp, (Lpar, Lperp)
+    assert Lpar > 0.5 * nx, Lpar                          # of the order of the system size
