@@ -86,6 +86,50 @@ __device__ __forceinline__ void dft8(C* v) {
   v[7] = csub(e3, t3);
 }
 
+// radix 16 as 4 x 4: radix-4 DFTs over n1 (n = 4 n1 + n2), the factors
+// w16^{n2 k1}, w16 = exp(sigma 2 pi i / 16), then radix-4 DFTs over n2;
+// X[k1 + 4 k2] lands in v[k1 + 4 k2]
+template <bool INV, class C>
+__device__ __forceinline__ C w16_times(C x, int e) {
+  using T = decltype(x.x);
+  const T c1 = T(0.92387953251128675612818318939678828682), s1 = T(0.38268343236508977172845998403039886676);
+  const T r2 = T(0.70710678118654752440084436210484903928);
+  const T sg = INV ? T(1) : T(-1);                     // sign of the imaginary part of w16
+  T cr, ci;                                            // w16^e = cr + i sg ci
+  switch (e) {
+    case 1: cr = c1; ci = s1; break;
+    case 2: cr = r2; ci = r2; break;
+    case 3: cr = s1; ci = c1; break;
+    case 4: return mul_si<INV>(x);
+    case 6: cr = -r2; ci = r2; break;
+    case 9: cr = -c1; ci = -s1; break;
+    default: return x;
+  }
+  const T wi = sg * ci;
+  return C{x.x * cr - x.y * wi, x.x * wi + x.y * cr};
+}
+template <bool INV, class C>
+__device__ __forceinline__ void dft16(C* v) {
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(v[n2], v[4 + n2], v[8 + n2], v[12 + n2]);   // -> v[4 k1 + n2]
+#pragma unroll
+  for (int n2 = 1; n2 < 4; ++n2)
+#pragma unroll
+    for (int k1 = 1; k1 < 4; ++k1) v[4 * k1 + n2] = w16_times<INV>(v[4 * k1 + n2], n2 * k1);
+  C o[16];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    C a = v[4 * k1], b = v[4 * k1 + 1], c = v[4 * k1 + 2], d = v[4 * k1 + 3];
+    dft4<INV>(a, b, c, d);
+    o[k1] = a;
+    o[k1 + 4] = b;
+    o[k1 + 8] = c;
+    o[k1 + 12] = d;
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) v[q] = o[q];
+}
+
 template <bool INV, class C>
 __device__ __forceinline__ C twiddle(const C* __restrict__ tw, int idx) {
   C w = __ldg(tw + idx);
@@ -222,11 +266,17 @@ __device__ __forceinline__ void load_stage_factors(const C* __restrict__ tab, in
     f[6] = cmul(f[4], w2);
     f[7] = cmul(f[4], f[3]);
   }
+  if (R > 8) {                                          // w8 = w4 w4, w(8+r) = w8 wr
+    f[8] = cmul(f[4], f[4]);
+#pragma unroll
+    for (int r = 1; r < 8; ++r) f[8 + r] = cmul(f[8], f[r]);
+  }
 }
 
 template <bool INV, int LR, class C>
 __device__ __forceinline__ void dft_radix(C* v) {
-  if (LR == 3) dft8<INV>(v);
+  if (LR == 4) dft16<INV>(v);
+  else if (LR == 3) dft8<INV>(v);
   else if (LR == 2) dft4<INV>(v[0], v[1], v[2], v[3]);
   else dft2<INV>(v[0], v[1]);
 }
@@ -234,12 +284,14 @@ __device__ __forceinline__ void dft_radix(C* v) {
 // One stage on the register layout.  LAST: keep the outputs in registers;
 // otherwise scatter them to buf (padded), barrier, gather the next stage's
 // inputs, barrier (so the buffer can be written again).
-template <bool INV, int LR, bool LAST, class C>
-__device__ __forceinline__ void fft_reg_stage(C (&v)[kP], int log2N, int log2Ns, int t, C* buf,
+template <int P> constexpr int log2_points() { return P == 16 ? 4 : 3; }
+
+template <bool INV, int LR, bool LAST, int P, class C>
+__device__ __forceinline__ void fft_reg_stage(C (&v)[P], int log2N, int log2Ns, int t, C* buf,
                                               const C* __restrict__ twt) {
   constexpr int R = 1 << LR;
-  constexpr int B = kP >> LR;
-  const int T = 1 << (log2N - kLogP);
+  constexpr int B = P >> LR;
+  const int T = 1 << (log2N - log2_points<P>());
   const int Ns = 1 << log2Ns;
   C w[R];
 #pragma unroll
@@ -267,7 +319,7 @@ __device__ __forceinline__ void fft_reg_stage(C (&v)[kP], int log2N, int log2Ns,
   if (!LAST) {
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < kP; ++q) v[q] = buf[pad16(t + q * T)];
+    for (int q = 0; q < P; ++q) v[q] = buf[pad16(t + q * T)];
     __syncthreads();
   }
 }
@@ -276,14 +328,16 @@ __device__ __forceinline__ void fft_reg_stage(C (&v)[kP], int log2N, int log2Ns,
 // buf: this instance's padded exchange buffer (padded_len(N) elements); tw:
 // the stage tables (stage_table_offset).  All threads of the CTA must call it
 // (barriers) with the same log2N.
-template <bool INV, class C>
-__device__ __forceinline__ void fft_reg(C (&v)[kP], int log2N, int t, C* buf, const C* __restrict__ tw) {
+template <bool INV, int P, class C>
+__device__ __forceinline__ void fft_reg(C (&v)[P], int log2N, int t, C* buf, const C* __restrict__ tw) {
+  constexpr int LP = log2_points<P>();
   int log2Ns = 0;
-  while (log2N - log2Ns > kLogP) {
-    fft_reg_stage<INV, kLogP, false>(v, log2N, log2Ns, t, buf, tw);
-    log2Ns += kLogP;
+  while (log2N - log2Ns > LP) {
+    fft_reg_stage<INV, LP, false>(v, log2N, log2Ns, t, buf, tw);
+    log2Ns += LP;
   }
   switch (log2N - log2Ns) {
+    case 4: if constexpr (P == 16) fft_reg_stage<INV, 4, true>(v, log2N, log2Ns, t, buf, tw); break;
     case 3: fft_reg_stage<INV, 3, true>(v, log2N, log2Ns, t, buf, tw); break;
     case 2: fft_reg_stage<INV, 2, true>(v, log2N, log2Ns, t, buf, tw); break;
     default: fft_reg_stage<INV, 1, true>(v, log2N, log2Ns, t, buf, tw); break;
@@ -364,11 +418,11 @@ __device__ __forceinline__ void fft_reg2(float2 (&a)[kP], float2 (&b)[kP], int l
 }
 
 // v[q] = X[t + T q] -> buf (padded, natural order), followed by a barrier.
-template <class C>
-__device__ __forceinline__ void reg_to_smem(const C (&v)[kP], int log2N, int t, C* buf) {
-  const int T = 1 << (log2N - kLogP);
+template <int P, class C>
+__device__ __forceinline__ void reg_to_smem(const C (&v)[P], int log2N, int t, C* buf) {
+  const int T = 1 << (log2N - log2_points<P>());
 #pragma unroll
-  for (int q = 0; q < kP; ++q) buf[pad16(t + q * T)] = v[q];
+  for (int q = 0; q < P; ++q) buf[pad16(t + q * T)] = v[q];
   __syncthreads();
 }
 

@@ -169,8 +169,11 @@ int sm_count() {
 template <class T>
 LaunchCfg persistent_cfg(int kind, int nfft, int max_inst, int items, size_t inst_bytes, int nmem) {
   LaunchCfg c{};
-  const int Tf = nfft / kP;
-  int ipc = 512 / Tf;
+  const bool fwd = kind == KIND_ROWFWD_PHI || kind == KIND_ROWFWD_G;
+  const int P = fwd ? rowfwd_points<T>() : kP;           // points per thread of the kind's transforms
+  const int cta = fwd ? rowfwd_cta_threads<T>() : 512;
+  const int Tf = nfft / P;
+  int ipc = cta / Tf;
   if (ipc < 1) ipc = 1;
   if (ipc > max_inst) ipc = max_inst;
   while (ipc > 1 && ipc * inst_bytes > kSmemLimit) ipc /= 2;

@@ -93,6 +93,13 @@ __host__ __device__ constexpr size_t rowinv_inst_bytes(int nx, size_t real_bytes
   return round128(((size_t)nx + (size_t)padded_len(nx)) * 2 * real_bytes);
 }
 
+// Points per thread of the forward row transforms (16: radix-16 stages, in
+// FP32) and threads per CTA of that pass; the inverse row and the column
+// passes use 8 points and 512 threads.
+template <class T> constexpr int rowfwd_points() { return sizeof(T) == 4 ? 16 : 8; }
+template <class T> constexpr int rowfwd_cta_threads() { return sizeof(T) == 4 ? 256 : 512; }
+template <class T> constexpr int rowfwd_min_ctas() { return sizeof(T) == 4 ? 3 : 1; }
+
 // The eight launches of a step, in order.
 enum StepKind {
   KIND_STENCIL1 = 0,

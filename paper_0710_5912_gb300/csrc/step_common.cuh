@@ -115,11 +115,11 @@ __device__ __forceinline__ void write_pair_rows(const C* z, C* dst, int j0, int 
 }
 
 // v[q] = Z[t + T q] from a padded buffer (the register layout of fft_reg)
-template <class C>
-__device__ __forceinline__ void smem_to_reg(C (&v)[kP], const C* Z, int log2N, int t) {
-  const int T = 1 << (log2N - kLogP);
+template <int P, class C>
+__device__ __forceinline__ void smem_to_reg(C (&v)[P], const C* Z, int log2N, int t) {
+  const int T = 1 << (log2N - log2_points<P>());
 #pragma unroll
-  for (int q = 0; q < kP; ++q) v[q] = Z[pad16(t + q * T)];
+  for (int q = 0; q < P; ++q) v[q] = Z[pad16(t + q * T)];
 }
 
 // Number of loop iterations of a persistent CTA: every instance of the CTA runs

@@ -12,7 +12,7 @@ namespace shf {
 // transforms a + i b (for f the staged phi rows are cubed on the fly), so every
 // output chunk of the pair is one whole 32-byte piece.
 template <class T, int LN>
-__global__ void __launch_bounds__(512, min_ctas<T>()) k_rowfwd(const MemberDesc* __restrict__ descs, int log2ny,
+__global__ void __launch_bounds__(rowfwd_cta_threads<T>(), rowfwd_min_ctas<T>()) k_rowfwd(const MemberDesc* __restrict__ descs, int log2ny,
                                                                const cplx<T>* __restrict__ tw, int mode) {
   constexpr int log2nx = LN;
   using C = cplx<T>;
@@ -20,7 +20,8 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_rowfwd(const MemberDesc*
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const MemberDesc& D = descs[blockIdx.y];
   const int nx = 1 << log2nx, ny = 1 << log2ny;
-  const int Tf = nx >> kLogP;
+  constexpr int P = rowfwd_points<T>();
+  const int Tf = nx / P;
   const int ipc = blockDim.x / Tf;
   const int inst = threadIdx.x / Tf, t = threadIdx.x - inst * Tf;
   const int nsub = mode == 0 ? (D.stokes ? 2 : 3) : 1;
@@ -64,9 +65,9 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_rowfwd(const MemberDesc*
     const bool cube = mode == 0 && sub == 1;
     cp_async_wait_all();
     __syncthreads();
-    C v[kP];
+    C v[P];
 #pragma unroll
-    for (int q = 0; q < kP; ++q) {
+    for (int q = 0; q < P; ++q) {
       const int i = t + q * Tf;
       const T a = stage[i], bb = stage[nx + i];
       v[q] = cube ? C{(a * a) * a, (bb * bb) * bb} : C{a, bb};
@@ -117,7 +118,8 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_rowinv(const MemberDesc*
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const MemberDesc& D = descs[blockIdx.y];
   const int nx = 1 << log2nx, ny = 1 << log2ny, mx = nx - 1;
-  const int Tf = nx >> kLogP;
+  constexpr int P = kP;
+  const int Tf = nx / P;
   const int ipc = blockDim.x / Tf;
   const int inst = threadIdx.x / Tf, t = threadIdx.x - inst * Tf;
   const int nsub = (mode == 1 && !D.stokes) ? 2 : 1;
@@ -175,15 +177,15 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_rowinv(const MemberDesc*
     }
     __syncthreads();                                    // Z complete, stage free
     issue(w + stride);
-    C v[kP];
+    C v[P];
     smem_to_reg(v, Z, log2nx, t);
     __syncthreads();                                    // Z becomes the exchange buffer
     // the real-space base of the increment (phi* or omega*), loaded before the transform
-    T b0[kP], b1[kP];
+    T b0[P], b1[P];
     if (active && kind != 1) {
       const T* bs = static_cast<const T*>(kind == 0 ? D.phi_star : D.omega_star);
 #pragma unroll
-      for (int q = 0; q < kP; ++q) {
+      for (int q = 0; q < P; ++q) {
         b0[q] = bs[((size_t)j0 << log2nx) + t + q * Tf];
         b1[q] = bs[((size_t)j1 << log2nx) + t + q * Tf];
       }
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_rowinv(const MemberDesc*
       if (kind == 1) {
         T* out = static_cast<T*>(D.psi);
 #pragma unroll
-        for (int q = 0; q < kP; ++q) {
+        for (int q = 0; q < P; ++q) {
           out[((size_t)j0 << log2nx) + t + q * Tf] = v[q].x;
           out[((size_t)j1 << log2nx) + t + q * Tf] = v[q].y;
         }
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_rowinv(const MemberDesc*
         const int sh0 = (kind == 0 && dK) ? remap_shift(dK, D.ratio, j0, nx) : 0;
         const int sh1 = (kind == 0 && dK) ? remap_shift(dK, D.ratio, j1, nx) : 0;
 #pragma unroll
-        for (int q = 0; q < kP; ++q) {
+        for (int q = 0; q < P; ++q) {
           const int i = t + q * Tf;
           out[((size_t)j0 << log2nx) + ((i + sh0) & mx)] = b0[q] + v[q].x;
           out[((size_t)j1 << log2nx) + ((i + sh1) & mx)] = b1[q] + v[q].y;
