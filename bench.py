@@ -67,6 +67,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     return ap.parse_args()
 
 
@@ -362,6 +363,31 @@ def main():
                 "fp32_vs_fp64_rel_l2_after_200_steps": errs,
                 "stated_tolerance": "FP32 <= 2e-5, FP64 <= 1e-10 relative L2 vs the FP64 oracle after 200 steps"}
 
+    # the batched ensemble (96 runs: 32 each of 128^2, 256^2, 512^2; rho = r mod 2;
+    # gdot log-spaced 1e-4..3e-2) through its graph path, 100 steps per replay
+    ensemble = None
+    if not args.no_ensemble:
+        nxs = [128 * 2 ** (r // 32) for r in range(96)]
+        eparams = [[1.0, 1.0, 1.0, 1.0, 1.0, float(r % 2), 1e-4 * 300.0 ** (r / 95.0), PARAMS["dt"]]
+                   for r in range(96)]
+        ens = shf.Ensemble(nxs, nxs, eparams, seeds=list(range(96)), amp=AMP, precision=shf.SHF_FP32,
+                           stream=stream)
+        ens.step(100)                                   # warm-up (captures the graph)
+        ens.sync()
+        ne = 200
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ens.step(ne)
+        e1.record(stream)
+        e1.synchronize()
+        ems = e0.elapsed_time(e1) / ne
+        pts = sum(n * n for n in nxs)
+        ensemble = {"value": world * pts / (allreduce_max(ems, world) / 1e3), "unit": UNIT, "ms_per_step": ems,
+                    "runs": 96, "points_per_step": pts, "steps": ne,
+                    "workload": "96 runs (32 x 128^2, 32 x 256^2, 32 x 512^2), FP32, rho = r mod 2, "
+                                "gdot = 1e-4 * 300^(r/95), seeds 0..95, graph replay of 100 steps"}
+        ens.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, secs = cpu_oracle_step_rate(NX, 1)
@@ -382,7 +408,7 @@ def main():
                 "graph_ms_per_step": graph_ms_per_step,
                 "step_algorithmic_bytes": step_bytes,
                 "step_hbm_frac": step_bytes / (ms_per_step * 1e-3) / 1e9 / peak,
-                "kernels": kernels, "fp64": fp64}
+                "kernels": kernels, "fp64": fp64, "ensemble": ensemble}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

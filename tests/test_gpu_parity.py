@@ -347,6 +347,33 @@ def test_ensemble_members_match_single_runs(prec):
     ens.close()
 
 
+def c4_ensemble_spec():
+    """The batched-ensemble configuration: 96 runs, 32 each of 128^2, 256^2 and
+    512^2, rho = r mod 2, gdot log-spaced over 1e-4 .. 3e-2, seed r."""
+    nxs = [128 * 2 ** (r // 32) for r in range(96)]
+    params = [[1.0, 1.0, 1.0, 1.0, 1.0, float(r % 2), 1e-4 * 300.0 ** (r / 95.0), 0.005] for r in range(96)]
+    return nxs, params
+
+
+def test_c4_ensemble_members_match_single_runs_and_oracle():
+    nxs, params = c4_ensemble_spec()
+    ens = shf.Ensemble(nxs, nxs, params, seeds=list(range(96)), amp=0.01, precision=FP32)
+    ens.step(20)
+    ens.sync()
+    for r in (0, 33, 95):
+        a, b, kap, M, eta, rho, gdot, dt = params[r]
+        p = oracle.Params(a=a, b=b, kappa=kap, M=M, eta=eta, rho=rho, gdot=gdot, dt=dt)
+        fields = inputs.quench_state(nxs[r], nxs[r], r, 0.01)
+        single = gpu_run(nxs[r], nxs[r], FP32, p, fields, 0, 20)
+        got = ens.members[r].get_fields()
+        for x, y in zip(got, single):
+            assert np.array_equal(x, y), f"member {r}"
+        if nxs[r] <= 256:
+            want = oracle_run(p, fields, 0, 20)
+            assert_close(got, want, 1e-5, rho, f"C4 member {r}", FP32, oracle.strain(20, gdot, dt, nxs[r], nxs[r])[0])
+    ens.close()
+
+
 # --------------------------------------------------------------- diagnostics
 
 @pytest.mark.parametrize("prec,tol", [(FP64, 1e-11), (FP32, 1e-5)])
