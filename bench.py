@@ -263,6 +263,7 @@ def main():
     g = shf.Grid(NX, NY, 1.0, shf.SHF_FP32, stream=stream)
     g.set_params(**PARAMS)
     g.init_noise(SEED + rank, AMP)
+    tuned = g.autotune()                                # launch variants timed on this GPU
     if args.warmup > 0:
         g.profile_step(args.warmup)
     g.sync()
@@ -407,7 +408,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, **PARAMS, "seed": SEED, "amp": AMP,
                            "parallelism": f"replicas x{world}" if world > 1 else "single grid",
-                           "l2": "state + scratch 576 MiB > L2 (129 MB): inputs larger than L2, no flush"},
+                           "l2": "state + scratch 576 MiB > L2 (129 MB): inputs larger than L2, no flush",
+                           "autotuned": {"rowfwd_points": tuned[0][0], "stencil_rows": tuned[0][1]}},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e,
                 # eight step kernels per step plus the one state-seeding launch of the run
                 "gpu_launches": len(KERNEL_REALS_PER_POINT) * args.steps + 1,

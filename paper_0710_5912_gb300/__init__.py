@@ -173,6 +173,15 @@ def shf_gradient_tensor(h):
     return tuple(G), tuple(L)
 
 
+def shf_autotune(h, cache_path=None, nclasses=8):
+    """Tune the launch variants per size class; returns [(rowfwd_points, stencil_rows), ...]."""
+    out = (ctypes.c_int * (2 * nclasses))()
+    path = None if cache_path is None else str(cache_path).encode()
+    _check(lib().shf_autotune(h, path, out, 2 * nclasses), h, "shf_autotune")
+    pairs = [(out[2 * c], out[2 * c + 1]) for c in range(nclasses)]
+    return [p for p in pairs if p[0] > 0]
+
+
 def shf_structure_factor(h, nbins=0):
     moments = np.zeros(5)
     bins = np.zeros(max(int(nbins), 1))
@@ -270,6 +279,9 @@ class Grid:
     def gradient_tensor(self):
         return shf_gradient_tensor(self.handle)
 
+    def autotune(self, cache_path=None):
+        return shf_autotune(self.handle, cache_path)
+
     def save(self, path):
         shf_save(self.handle, path)
 
@@ -330,6 +342,9 @@ class Ensemble:
 
     def step(self, nsteps=1):
         shf_step(self.handle, nsteps)
+
+    def autotune(self, cache_path=None):
+        return shf_autotune(self.handle, cache_path)
 
     def sync(self):
         shf_sync(self.handle)

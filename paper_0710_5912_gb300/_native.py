@@ -132,6 +132,7 @@ SIGNATURES = {
     "shf_mass": (c_int, [c_void_p, P_double]),
     "shf_structure_factor": (c_int, [c_void_p, P_double, c_int, P_double]),
     "shf_gradient_tensor": (c_int, [c_void_p, P_double, P_double]),
+    "shf_autotune": (c_int, [c_void_p, c_char_p, P_int, c_int]),
     "shf_save": (c_int, [c_void_p, c_char_p]),
     "shf_load": (c_int, [c_void_p, c_char_p]),
     "shf_create_ensemble": (c_int, [P_void_p, c_int, P_int, P_int, P_double, P_double, P_uint64, c_double,

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstddef>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -163,15 +164,15 @@ int sm_count() {
   return sms > 0 ? sms : 1;
 }
 
-// Persistent transform kernels: nfft/8 threads per instance, instances per
-// CTA up to 512 threads; the grid holds as many CTAs as are resident at once
-// (occupancy query), shared over the members of the launch.
+// Persistent transform kernels: nfft/P threads per instance (P points per
+// thread: 8, or the forward rows' variant), instances per CTA up to the kind's
+// CTA size; the grid holds as many CTAs as are resident at once (occupancy
+// query), shared over the members of the launch.
 template <class T>
-LaunchCfg persistent_cfg(int kind, int nfft, int max_inst, int items, size_t inst_bytes, int nmem) {
+LaunchCfg persistent_cfg(int kind, int nfft, int max_inst, int items, size_t inst_bytes, int nmem, int P = kP) {
   LaunchCfg c{};
   const bool fwd = kind == KIND_ROWFWD_PHI || kind == KIND_ROWFWD_G;
-  const int P = fwd ? rowfwd_points<T>() : kP;           // points per thread of the kind's transforms
-  const int cta = fwd ? rowfwd_cta_threads<T>() : 512;
+  const int cta = fwd ? rowfwd_cta_threads(P) : 512;
   const int Tf = nfft / P;
   int ipc = cta / Tf;
   if (ipc < 1) ipc = 1;
@@ -180,10 +181,11 @@ LaunchCfg persistent_cfg(int kind, int nfft, int max_inst, int items, size_t ins
   c.inst_per_cta = ipc;
   c.threads = ipc * Tf;
   c.smem = ipc * inst_bytes;
+  c.variant = fwd ? P : 0;
   const int work = (items + ipc - 1) / ipc;
   int log2n = 0;
   while ((1 << log2n) < nfft) ++log2n;
-  const int resident = step_kernel_occupancy<T>(kind, log2n, c.threads, c.smem) * sm_count();
+  const int resident = step_kernel_occupancy<T>(kind, log2n, c.variant, c.threads, c.smem) * sm_count();
   int g = (resident + nmem - 1) / nmem;
   if (g > work) g = work;
   c.grid_x = g < 1 ? 1 : g;
@@ -191,23 +193,42 @@ LaunchCfg persistent_cfg(int kind, int nfft, int max_inst, int items, size_t ins
   return c;
 }
 
+// The tuning knobs of a size class: points per thread of the forward row
+// transforms (8 or 16; FP64: 8) and the stencil tile height (16 or 32, at
+// most ny).  Zero means "the default".
+struct Tune {
+  int rowfwd_points = 0;
+  int stencil_rows = 0;
+};
+
 template <class T>
-void configure_class_t(SizeClass& cl) {
+Tune resolved(const SizeClass& cl, Tune t) {
+  if (t.rowfwd_points == 0 || sizeof(T) == 8) t.rowfwd_points = rowfwd_default_points<T>();
+  const int maxrows = cl.ny < 32 ? cl.ny : 32;
+  if (t.stencil_rows == 0 || t.stencil_rows > maxrows) t.stencil_rows = maxrows;
+  return t;
+}
+
+template <class T>
+void configure_class_t(SizeClass& cl, Tune tune) {
+  tune = resolved<T>(cl, tune);
   const size_t R = sizeof(T), Cx = 2 * R;
   const int nx = cl.nx, ny = cl.ny, nmem = (int)cl.members.size();
-  // stencil tiles of TX = min(nx, 128) by TY = min(ny, 32), 4 x 4 outputs per thread
-  const int TX = nx < 128 ? nx : 128, TY = ny < 32 ? ny : 32;
+  // stencil tiles of TX = min(nx, 128) by TY rows, 4 x 4 outputs per thread
+  const int TX = nx < 128 ? nx : 128, TY = tune.stencil_rows;
   LaunchCfg st{};
   st.grid_x = nx / TX;
   st.grid_y = ny / TY;
   st.threads = (TX / 4) * (TY / 4);
+  st.variant = TY;
   st.smem = stencil1_smem_bytes(TX, TY, R);
   cl.cfg[KIND_STENCIL1] = st;
   st.smem = stencil2_smem_bytes(TX, TY, R);
   cl.cfg[KIND_STENCIL2] = st;
+  const int P = tune.rowfwd_points;
   cl.cfg[KIND_ROWFWD_PHI] =
-      persistent_cfg<T>(KIND_ROWFWD_PHI, nx, ny / 2, 3 * (ny / 2), rowfwd_inst_bytes(nx, R), nmem);
-  cl.cfg[KIND_ROWFWD_G] = persistent_cfg<T>(KIND_ROWFWD_G, nx, ny / 2, ny / 2, rowfwd_inst_bytes(nx, R), nmem);
+      persistent_cfg<T>(KIND_ROWFWD_PHI, nx, ny / 2, 3 * (ny / 2), rowfwd_inst_bytes(nx, R), nmem, P);
+  cl.cfg[KIND_ROWFWD_G] = persistent_cfg<T>(KIND_ROWFWD_G, nx, ny / 2, ny / 2, rowfwd_inst_bytes(nx, R), nmem, P);
   // column items: whole 16-byte chunks (two modes in FP32, one in FP64)
   const int ncol_items = R == 4 ? nx / 4 : nx / 2;
   cl.cfg[KIND_COLPASS_PHI] =
@@ -220,9 +241,9 @@ void configure_class_t(SizeClass& cl) {
   cl.sfcols = sf_col_cfg(nx, ny, Cx + 12, Cx);
 }
 
-void configure_class(SizeClass& cl, int precision) {
-  if (precision == SHF_FP64) configure_class_t<double>(cl);
-  else configure_class_t<float>(cl);
+void configure_class(SizeClass& cl, int precision, Tune tune = Tune{}) {
+  if (precision == SHF_FP64) configure_class_t<double>(cl, tune);
+  else configure_class_t<float>(cl, tune);
 }
 
 void host_strain(long long n, double gdot, double dt, int r, double* s, long long* K) {
@@ -652,6 +673,118 @@ int sf_sums(shf_grid* g, double* S_binned, int nbins, double sums[kSfMoments]) {
 
 }  // namespace
 
+// ------------------------------------------------------------- autotuning
+namespace {
+
+std::string tune_key(const shf_grid* o, const SizeClass& cl) {
+  bool inertial = false, stokes = false;
+  for (int r : cl.members) (o->members[r].rho > 0 ? inertial : stokes) = true;
+  char buf[96];
+  std::snprintf(buf, sizeof(buf), "%dx%d:%s:%s", cl.nx, cl.ny, o->precision == SHF_FP64 ? "fp64" : "fp32",
+                inertial && stokes ? "mixed" : (inertial ? "inertial" : "stokes"));
+  return buf;
+}
+
+// cache file: a JSON object, one entry per line:
+//   "NXxNY:fp32:inertial": {"rowfwd_points": 16, "stencil_rows": 32},
+std::map<std::string, Tune> read_tune_cache(const char* path) {
+  std::map<std::string, Tune> m;
+  if (!path) return m;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return m;
+  char line[512];
+  while (std::fgets(line, sizeof(line), f)) {
+    char key[256];
+    Tune t;
+    if (std::sscanf(line, " \"%255[^\"]\": {\"rowfwd_points\": %d, \"stencil_rows\": %d", key, &t.rowfwd_points,
+                    &t.stencil_rows) == 3)
+      m[key] = t;
+  }
+  std::fclose(f);
+  return m;
+}
+
+bool write_tune_cache(const char* path, const std::map<std::string, Tune>& m) {
+  FILE* f = std::fopen(path, "w");
+  if (!f) return false;
+  std::fprintf(f, "{\n");
+  size_t i = 0;
+  for (const auto& kv : m) {
+    std::fprintf(f, "  \"%s\": {\"rowfwd_points\": %d, \"stencil_rows\": %d}%s\n", kv.first.c_str(),
+                 kv.second.rowfwd_points, kv.second.stencil_rows, ++i < m.size() ? "," : "");
+  }
+  std::fprintf(f, "}\n");
+  return std::fclose(f) == 0;
+}
+
+// mean device time (ms) of one round of the given kinds of class cl
+template <class T>
+int time_kinds(shf_grid* o, SizeClass& cl, const int* kinds, int nk, float* ms) {
+  const int reps = 5;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return SHF_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return SHF_ECUDA;
+  }
+  for (int k = 0; k < nk; ++k) launch_kind<T>(o, cl, kinds[k]);   // warm-up
+  cudaEventRecord(e0, o->stream);
+  for (int r = 0; r < reps; ++r)
+    for (int k = 0; k < nk; ++k) launch_kind<T>(o, cl, kinds[k]);
+  cudaEventRecord(e1, o->stream);
+  cudaError_t err = cudaGetLastError();
+  if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+  if (err == cudaSuccess) err = cudaEventElapsedTime(ms, e0, e1);
+  *ms /= reps;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return err == cudaSuccess ? SHF_OK : SHF_ECUDA;
+}
+
+// Time the candidate values of each knob on the class's own buffers.  Only
+// kinds that write scratch (stencils: phi*, omega*, g; forward rows: the
+// x-spectral buffers) run, so the state (phi, psi, omega, step) is untouched.
+template <class T>
+int tune_class(shf_grid* o, SizeClass& cl, Tune* best) {
+  Tune t = resolved<T>(cl, Tune{});
+  if (sizeof(T) == 4) {
+    const int fwd[2] = {KIND_ROWFWD_PHI, KIND_ROWFWD_G};
+    float bestms = 0.f;
+    for (int P : {8, 16}) {
+      Tune c = t;
+      c.rowfwd_points = P;
+      configure_class_t<T>(cl, c);
+      float ms = 0.f;
+      const int rc = time_kinds<T>(o, cl, fwd, 2, &ms);
+      if (rc) return rc;
+      if (P == 8 || ms < bestms) {
+        bestms = ms;
+        t.rowfwd_points = P;
+      }
+    }
+  }
+  if (cl.ny >= 32) {
+    const int st[2] = {KIND_STENCIL1, KIND_STENCIL2};
+    float bestms = 0.f;
+    for (int TY : {16, 32}) {
+      Tune c = t;
+      c.stencil_rows = TY;
+      configure_class_t<T>(cl, c);
+      float ms = 0.f;
+      const int rc = time_kinds<T>(o, cl, st, 2, &ms);
+      if (rc) return rc;
+      if (TY == 16 || ms < bestms) {
+        bestms = ms;
+        t.stencil_rows = TY;
+      }
+    }
+  }
+  *best = t;
+  return SHF_OK;
+}
+
+}  // namespace
+
 // =========================================================================
 extern "C" {
 
@@ -951,6 +1084,48 @@ int shf_profile_step(shf_grid* g, int64_t nsteps, double* kernel_ms, int nkinds)
   for (cudaEvent_t e : ev)
     if (e) cudaEventDestroy(e);
   return rc;
+}
+
+
+int shf_autotune(shf_grid* g, const char* cache_path, int* choices, int nchoices) {
+  if (!g || nchoices < 0 || (nchoices > 0 && !choices)) return fail(g, SHF_EINVAL, "bad autotune arguments");
+  if (g->kind == 2) return fail(g, SHF_EINVAL, "tune the ensemble, not a member view");
+  for (auto& m : g->members)
+    if (!m.params_set) return fail(g, SHF_ESTATE, "shf_set_params must be called before shf_autotune");
+  SHF_CUDA(g, cudaSetDevice(g->device));
+  SHF_CUDA(g, cudaStreamSynchronize(g->stream));
+  std::map<std::string, Tune> cache = read_tune_cache(cache_path);
+  bool changed = false;
+  enqueue_state_init(g);                                // the stencils read the step's strain
+  for (size_t c = 0; c < g->classes.size(); ++c) {
+    SizeClass& cl = g->classes[c];
+    const std::string key = tune_key(g, cl);
+    Tune t;
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      t = it->second;
+    } else {
+      const int rc = g->precision == SHF_FP64 ? tune_class<double>(g, cl, &t) : tune_class<float>(g, cl, &t);
+      if (rc) return fail(g, rc, "autotune: a trial launch failed");
+      cache[key] = t;
+      changed = true;
+    }
+    configure_class(cl, g->precision, t);
+    if (g->precision == SHF_FP64) t = resolved<double>(cl, t);
+    else t = resolved<float>(cl, t);
+    if ((int)(2 * c + 1) < nchoices) {
+      choices[2 * c] = t.rowfwd_points;
+      choices[2 * c + 1] = t.stencil_rows;
+    }
+  }
+  if (g->graph) {                                       // re-captured with the new launch shapes
+    cudaGraphExecDestroy(g->graph);
+    g->graph = nullptr;
+  }
+  SHF_CUDA(g, cudaStreamSynchronize(g->stream));
+  if (cache_path && changed && !write_tune_cache(cache_path, cache))
+    return fail(g, SHF_EIO, std::string("autotune: cannot write ") + cache_path);
+  return SHF_OK;
 }
 
 int shf_sync(shf_grid* g) {

@@ -93,12 +93,14 @@ __host__ __device__ constexpr size_t rowinv_inst_bytes(int nx, size_t real_bytes
   return round128(((size_t)nx + (size_t)padded_len(nx)) * 2 * real_bytes);
 }
 
-// Points per thread of the forward row transforms (16: radix-16 stages, in
-// FP32) and threads per CTA of that pass; the inverse row and the column
-// passes use 8 points and 512 threads.
-template <class T> constexpr int rowfwd_points() { return sizeof(T) == 4 ? 16 : 8; }
-template <class T> constexpr int rowfwd_cta_threads() { return sizeof(T) == 4 ? 256 : 512; }
-template <class T> constexpr int rowfwd_min_ctas() { return sizeof(T) == 4 ? 3 : 1; }
+// Forward row transforms come in two variants, P = 8 points per thread
+// (radix-8 stages, 512-thread CTAs) and P = 16 (radix-16 stages, 256-thread
+// CTAs, FP32 only); the inverse row and the column passes use 8 points and 512
+// threads.  The default P and the stencil tile height are tuning knobs
+// (shf_autotune).
+constexpr int rowfwd_cta_threads(int P) { return P == 16 ? 256 : 512; }
+template <class T> constexpr int rowfwd_min_ctas(int P) { return P == 16 ? 3 : (sizeof(T) == 4 ? 2 : 1); }
+template <class T> constexpr int rowfwd_default_points() { return sizeof(T) == 4 ? 16 : 8; }
 
 // The eight launches of a step, in order.
 enum StepKind {
@@ -118,17 +120,18 @@ struct LaunchCfg {
   int threads;
   size_t smem;          // dynamic shared memory bytes
   int inst_per_cta;     // transform instances per CTA (persistent kinds)
+  int variant;          // forward rows: points per thread (8, 16); stencils: tile rows (16, 32)
 };
 
 template <class T> void launch_step_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int log2ny,
                                            const cplx<T>* tw, const LaunchCfg& c, cudaStream_t st);
-template <class T> int step_kernel_occupancy(int kind, int log2n, int threads, size_t smem);
+template <class T> int step_kernel_occupancy(int kind, int log2n, int variant, int threads, size_t smem);
 // the transform kernels by family (step_rows.cu, step_cols.cu)
 template <class T> void launch_row_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int log2ny,
                                           const cplx<T>* tw, const LaunchCfg& c, cudaStream_t st);
 template <class T> void launch_col_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int log2ny,
                                           const cplx<T>* tw, const LaunchCfg& c, cudaStream_t st);
-template <class T> int row_kernel_occupancy(int kind, int log2nx, int threads, size_t smem);
+template <class T> int row_kernel_occupancy(int kind, int log2nx, int variant, int threads, size_t smem);
 template <class T> int col_kernel_occupancy(int log2ny, int threads, size_t smem);
 template <class T> void set_row_smem_limits(int lim);
 template <class T> void set_col_smem_limits(int lim);

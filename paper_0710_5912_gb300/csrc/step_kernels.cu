@@ -387,10 +387,11 @@ void launch_stencil_ty(int which, const MemberDesc* d, int nmem, int log2nx, int
     default: launch_stencil_t<T, 128, TY>(which, d, nmem, log2nx, log2ny, c, st); break;
   }
 }
+// the tile height TY (16 or 32, at most ny) is the launch's variant
 template <class T>
 void launch_stencil(int which, const MemberDesc* d, int nmem, int log2nx, int log2ny, const LaunchCfg& c,
                     cudaStream_t st) {
-  if (log2ny >= 5) launch_stencil_ty<T, 32>(which, d, nmem, log2nx, log2ny, c, st);
+  if (c.variant == 32) launch_stencil_ty<T, 32>(which, d, nmem, log2nx, log2ny, c, st);
   else launch_stencil_ty<T, 16>(which, d, nmem, log2nx, log2ny, c, st);
 }
 
@@ -409,9 +410,9 @@ void launch_step_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int
 // CTAs of a persistent kind that fit on one SM at (threads, smem); log2n is the
 // kind's transform length (log2 nx for row kinds, log2 ny for column kinds)
 template <class T>
-int step_kernel_occupancy(int kind, int log2n, int threads, size_t smem) {
+int step_kernel_occupancy(int kind, int log2n, int variant, int threads, size_t smem) {
   if (kind == KIND_COLPASS_PHI || kind == KIND_COLPASS_FLOW) return col_kernel_occupancy<T>(log2n, threads, smem);
-  return row_kernel_occupancy<T>(kind, log2n, threads, smem);
+  return row_kernel_occupancy<T>(kind, log2n, variant, threads, smem);
 }
 
 template <class T>
@@ -426,7 +427,7 @@ void set_step_smem_limits() {
 #define SHF_INST(T)                                                                                      \
   template void launch_step_kernel<T>(int, const MemberDesc*, int, int, int, const cplx<T>*,             \
                                       const LaunchCfg&, cudaStream_t);                                    \
-  template int step_kernel_occupancy<T>(int, int, int, size_t);                                           \
+  template int step_kernel_occupancy<T>(int, int, int, int, size_t);                                      \
   template void set_step_smem_limits<T>();
 
 SHF_INST(float)

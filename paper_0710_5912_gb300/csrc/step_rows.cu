@@ -11,8 +11,8 @@ namespace shf {
 // per row pair.  Each item stages the two real rows (a, b) in shared memory and
 // transforms a + i b (for f the staged phi rows are cubed on the fly), so every
 // output chunk of the pair is one whole 32-byte piece.
-template <class T, int LN>
-__global__ void __launch_bounds__(rowfwd_cta_threads<T>(), rowfwd_min_ctas<T>()) k_rowfwd(const MemberDesc* __restrict__ descs, int log2ny,
+template <class T, int LN, int P>
+__global__ void __launch_bounds__(rowfwd_cta_threads(P), rowfwd_min_ctas<T>(P)) k_rowfwd(const MemberDesc* __restrict__ descs, int log2ny,
                                                                const cplx<T>* __restrict__ tw, int mode) {
   constexpr int log2nx = LN;
   using C = cplx<T>;
@@ -20,7 +20,6 @@ __global__ void __launch_bounds__(rowfwd_cta_threads<T>(), rowfwd_min_ctas<T>())
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const MemberDesc& D = descs[blockIdx.y];
   const int nx = 1 << log2nx, ny = 1 << log2ny;
-  constexpr int P = rowfwd_points<T>();
   const int Tf = nx / P;
   const int ipc = blockDim.x / Tf;
   const int inst = threadIdx.x / Tf, t = threadIdx.x - inst * Tf;
@@ -218,27 +217,42 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_rowinv(const MemberDesc*
 }
 
 // ----------------------------------------------------------------- launchers
+// the forward-row kernel of variant P (points per thread); FP64 has P = 8 only
+template <class T, int LN>
+const void* rowfwd_fn(int P) {
+  if constexpr (sizeof(T) == 4) {
+    if (P == 16) return (const void*)k_rowfwd<T, LN, 16>;
+  }
+  return (const void*)k_rowfwd<T, LN, 8>;
+}
+
 template <class T>
 void launch_row_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int log2ny, const cplx<T>* tw,
                        const LaunchCfg& c, cudaStream_t st) {
   const dim3 grid(c.grid_x, nmem);
   with_log2n(log2nx, [&](auto L) {
     constexpr int LN = decltype(L)::value;
-    switch (kind) {
-      case KIND_ROWFWD_PHI: k_rowfwd<T, LN><<<grid, c.threads, c.smem, st>>>(d, log2ny, tw, 0); break;
-      case KIND_ROWFWD_G: k_rowfwd<T, LN><<<grid, c.threads, c.smem, st>>>(d, log2ny, tw, 1); break;
-      case KIND_ROWINV_PHI: k_rowinv<T, LN><<<grid, c.threads, c.smem, st>>>(d, log2ny, tw, 0); break;
-      default: k_rowinv<T, LN><<<grid, c.threads, c.smem, st>>>(d, log2ny, tw, 1); break;
+    const int mode = (kind == KIND_ROWFWD_PHI || kind == KIND_ROWINV_PHI) ? 0 : 1;
+    if (kind == KIND_ROWFWD_PHI || kind == KIND_ROWFWD_G) {
+      if constexpr (sizeof(T) == 4) {
+        if (c.variant == 16) {
+          k_rowfwd<T, LN, 16><<<grid, c.threads, c.smem, st>>>(d, log2ny, tw, mode);
+          return;
+        }
+      }
+      k_rowfwd<T, LN, 8><<<grid, c.threads, c.smem, st>>>(d, log2ny, tw, mode);
+    } else {
+      k_rowinv<T, LN><<<grid, c.threads, c.smem, st>>>(d, log2ny, tw, mode);
     }
   });
 }
 
 template <class T>
-int row_kernel_occupancy(int kind, int log2nx, int threads, size_t smem) {
+int row_kernel_occupancy(int kind, int log2nx, int variant, int threads, size_t smem) {
   int nb = 0;
   with_log2n(log2nx, [&](auto L) {
     constexpr int LN = decltype(L)::value;
-    const void* f = (kind == KIND_ROWFWD_PHI || kind == KIND_ROWFWD_G) ? (const void*)k_rowfwd<T, LN>
+    const void* f = (kind == KIND_ROWFWD_PHI || kind == KIND_ROWFWD_G) ? rowfwd_fn<T, LN>(variant)
                                                                         : (const void*)k_rowinv<T, LN>;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads, smem) != cudaSuccess) nb = 1;
   });
@@ -250,7 +264,8 @@ void set_row_smem_limits(int lim) {
   for (int ln = 4; ln <= LOG2_NMAX; ++ln)
     with_log2n(ln, [&](auto L) {
       constexpr int LN = decltype(L)::value;
-      cudaFuncSetAttribute(k_rowfwd<T, LN>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      cudaFuncSetAttribute(rowfwd_fn<T, LN>(8), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      cudaFuncSetAttribute(rowfwd_fn<T, LN>(16), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
       cudaFuncSetAttribute(k_rowinv<T, LN>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     });
 }
@@ -258,7 +273,7 @@ void set_row_smem_limits(int lim) {
 #define SHF_ROW_INST(T)                                                                                   \
   template void launch_row_kernel<T>(int, const MemberDesc*, int, int, int, const cplx<T>*, const LaunchCfg&, \
                                      cudaStream_t);                                                        \
-  template int row_kernel_occupancy<T>(int, int, int, size_t);                                             \
+  template int row_kernel_occupancy<T>(int, int, int, int, size_t);                                        \
   template void set_row_smem_limits<T>(int);
 
 SHF_ROW_INST(float)

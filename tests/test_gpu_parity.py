@@ -374,6 +374,52 @@ def test_c4_ensemble_members_match_single_runs_and_oracle():
     ens.close()
 
 
+def test_autotune_keeps_the_state_and_parity(tmp_path):
+    nx = ny = 256
+    p = oracle.Params(a=1, b=1, kappa=1, M=1, eta=1, rho=1.0, gdot=0.01, dt=0.005)
+    fields = inputs.quench_state(nx, ny, 6, 0.2)
+    cache = tmp_path / "tune.json"
+    with shf.Grid(nx, ny, 1.0, FP32) as g:
+        g.set_params(p.a, p.b, p.kappa, p.M, p.eta, p.rho, p.gdot, p.dt)
+        g.set_fields(*fields)
+        g.step(100)                                       # the graph path is captured before tuning
+        before = g.get_fields()
+        choices = g.autotune(cache)
+        assert len(choices) == 1 and choices[0][0] in (8, 16) and choices[0][1] in (16, 32)
+        after = g.get_fields()
+        for x, y in zip(before, after):
+            assert np.array_equal(x, y)                   # tuning runs only scratch-writing kernels
+        assert g.get_time()[0] == 100
+        g.step(100)                                       # graph re-captured with the tuned shapes
+        got = g.get_fields()
+    want = oracle_run(p, fields, 0, 200)
+    assert_close(got, want, 2e-5, 1.0, "autotuned 256^2", FP32, oracle.strain(200, p.gdot, p.dt, nx, ny)[0])
+    text = cache.read_text()
+    assert '"256x256:fp32:inertial"' in text
+    with shf.Grid(nx, ny, 1.0, FP32) as g2:                # the cached choice is applied as is
+        g2.set_params(p.a, p.b, p.kappa, p.M, p.eta, p.rho, p.gdot, p.dt)
+        assert g2.autotune(cache) == choices
+    assert cache.read_text() == text
+
+
+def test_autotune_ensemble_per_size_class():
+    nxs = [64, 128, 64, 128]
+    params = [[1.0, 1.0, 1.0, 1.0, 1.0, float(r % 2), 0.01, 0.005] for r in range(4)]
+    ens = shf.Ensemble(nxs, nxs, params, seeds=list(range(4)), amp=0.1, precision=FP32)
+    choices = ens.autotune()
+    assert len(choices) == 2
+    ens.step(20)
+    ens.sync()
+    for r in range(4):
+        a, b, kap, M, eta, rho, gdot, dt = params[r]
+        pr = oracle.Params(a=a, b=b, kappa=kap, M=M, eta=eta, rho=rho, gdot=gdot, dt=dt)
+        fields = inputs.quench_state(nxs[r], nxs[r], r, 0.1)
+        want = oracle_run(pr, fields, 0, 20)
+        assert_close(ens.members[r].get_fields(), want, 1e-5, rho, f"tuned member {r}", FP32,
+                     oracle.strain(20, gdot, dt, nxs[r], nxs[r])[0])
+    ens.close()
+
+
 # --------------------------------------------------------------- diagnostics
 
 @pytest.mark.parametrize("prec,tol", [(FP64, 1e-11), (FP32, 1e-5)])
