@@ -92,6 +92,12 @@ int shf_set_params(shf_grid* g, double a, double b, double kappa, double M, doub
  * (taken as zero).  For Stokes runs omega is ignored. */
 int shf_set_fields(shf_grid* g, const double* phi, const double* psi, const double* omega);
 
+/* The same as shf_set_fields / shf_get_fields with float host arrays, for
+ * FP32 grids only (SHF_EINVAL otherwise): the values are the grid's own, so
+ * nothing is converted and half the bytes cross the host link. */
+int shf_set_fields_f32(shf_grid* g, const float* phi, const float* psi, const float* omega);
+int shf_get_fields_f32(shf_grid* g, float* phi, float* psi, float* omega);
+
 /* phi = amp * (2u - 1) per point, u = (z >> 11) * 2^-53 from SplitMix64
  * (Steele, Lea & Flood 2014) started at seed, one draw per point in row-major
  * order; psi = omega = 0 (the quench of Section VII).  Also resets the step

@@ -173,6 +173,24 @@ def shf_gradient_tensor(h):
     return tuple(G), tuple(L)
 
 
+def _fptr(a):
+    return a.ctypes.data_as(_native.P_float) if a is not None else None
+
+
+def shf_set_fields_f32(h, nx, ny, phi, psi=None, omega=None):
+    arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float32) for a in (phi, psi, omega)]
+    for a in arrs:
+        if a is not None and a.shape != (ny, nx):
+            raise ValueError(f"field shape {a.shape} != ({ny}, {nx})")
+    _check(lib().shf_set_fields_f32(h, *[_fptr(a) for a in arrs]), h, "shf_set_fields_f32")
+
+
+def shf_get_fields_f32(h, nx, ny):
+    out = [np.empty((ny, nx), dtype=np.float32) for _ in range(3)]
+    _check(lib().shf_get_fields_f32(h, *[_fptr(a) for a in out]), h, "shf_get_fields_f32")
+    return tuple(out)
+
+
 def shf_autotune(h, cache_path=None, nclasses=8):
     """Tune the launch variants per size class; returns [(rowfwd_points, stencil_rows), ...]."""
     out = (ctypes.c_int * (2 * nclasses))()
@@ -266,6 +284,12 @@ class Grid:
 
     def get_fields(self):
         return shf_get_fields(self.handle, self.nx, self.ny)
+
+    def set_fields_f32(self, phi, psi=None, omega=None):
+        shf_set_fields_f32(self.handle, self.nx, self.ny, phi, psi, omega)
+
+    def get_fields_f32(self):
+        return shf_get_fields_f32(self.handle, self.nx, self.ny)
 
     def get_time(self):
         return shf_get_time(self.handle)

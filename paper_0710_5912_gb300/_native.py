@@ -106,6 +106,7 @@ def load(auto_build: bool = True) -> ctypes.CDLL:
 c_int, c_double, c_int64, c_uint64, c_void_p, c_char_p = (ctypes.c_int, ctypes.c_double, ctypes.c_int64,
                                                           ctypes.c_uint64, ctypes.c_void_p, ctypes.c_char_p)
 P_double = ctypes.POINTER(ctypes.c_double)
+P_float = ctypes.POINTER(ctypes.c_float)
 P_int = ctypes.POINTER(ctypes.c_int)
 P_int64 = ctypes.POINTER(ctypes.c_int64)
 P_uint64 = ctypes.POINTER(ctypes.c_uint64)
@@ -121,6 +122,8 @@ SIGNATURES = {
     "shf_set_params": (c_int, [c_void_p, c_double, c_double, c_double, c_double, c_double, c_double,
                                c_double, c_double]),
     "shf_set_fields": (c_int, [c_void_p, P_double, P_double, P_double]),
+    "shf_set_fields_f32": (c_int, [c_void_p, P_float, P_float, P_float]),
+    "shf_get_fields_f32": (c_int, [c_void_p, P_float, P_float, P_float]),
     "shf_init_noise": (c_int, [c_void_p, c_uint64, c_double]),
     "shf_bind_device_fields": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "shf_set_step": (c_int, [c_void_p, c_int64]),

@@ -578,6 +578,16 @@ int set_fields_t(shf_grid* g, const double* phi, const double* psi, const double
   const size_t count = (size_t)m.nx * m.ny;
   const double* src[3] = {phi, psi, m.rho > 0 ? omega : nullptr};
   void* dst[3] = {m.phi, m.psi, m.omega};
+  if (sizeof(T) != sizeof(double)) {
+    // all copies first (the copy engine streams without waiting for the
+    // conversions), then the conversions; one staging slot per field
+    int rc = ensure_stage(o, 3 * count);
+    if (rc) return fail(g, rc, o->err);
+    for (int f = 0; f < 3; ++f)
+      if (src[f])
+        SHF_CUDA(g, cudaMemcpyAsync(o->d_stage + f * count, src[f], count * sizeof(double), cudaMemcpyHostToDevice,
+                                    o->stream));
+  }
   for (int f = 0; f < 3; ++f) {
     if (!src[f]) {
       SHF_CUDA(g, cudaMemsetAsync(dst[f], 0, count * sizeof(T), o->stream));
@@ -586,10 +596,7 @@ int set_fields_t(shf_grid* g, const double* phi, const double* psi, const double
     if (sizeof(T) == sizeof(double)) {
       SHF_CUDA(g, cudaMemcpyAsync(dst[f], src[f], count * sizeof(double), cudaMemcpyHostToDevice, o->stream));
     } else {
-      int rc = ensure_stage(o, count);
-      if (rc) return fail(g, rc, o->err);
-      SHF_CUDA(g, cudaMemcpyAsync(o->d_stage, src[f], count * sizeof(double), cudaMemcpyHostToDevice, o->stream));
-      launch_convert_in<T>(o->d_stage, static_cast<T*>(dst[f]), (long long)count, o->stream);
+      launch_convert_in<T>(o->d_stage + f * count, static_cast<T*>(dst[f]), (long long)count, o->stream);
       SHF_CUDA(g, cudaGetLastError());
     }
   }
@@ -604,6 +611,11 @@ int get_fields_t(shf_grid* g, double* phi, double* psi, double* omega) {
   const size_t count = (size_t)m.nx * m.ny;
   double* dst[3] = {phi, psi, omega};
   const void* src[3] = {m.phi, m.psi, m.omega};
+  if (sizeof(T) != sizeof(double)) {
+    int rc = ensure_stage(o, 3 * count);
+    if (rc) return fail(g, rc, o->err);
+  }
+  // conversions and copies queue back to back (one staging slot per field)
   for (int f = 0; f < 3; ++f) {
     if (!dst[f]) continue;
     if (f == 2 && m.rho == 0.0) {
@@ -613,13 +625,11 @@ int get_fields_t(shf_grid* g, double* phi, double* psi, double* omega) {
     if (sizeof(T) == sizeof(double)) {
       SHF_CUDA(g, cudaMemcpyAsync(dst[f], src[f], count * sizeof(double), cudaMemcpyDeviceToHost, o->stream));
     } else {
-      int rc = ensure_stage(o, count);
-      if (rc) return fail(g, rc, o->err);
-      launch_convert_out<T>(static_cast<const T*>(src[f]), o->d_stage, (long long)count, o->stream);
+      launch_convert_out<T>(static_cast<const T*>(src[f]), o->d_stage + f * count, (long long)count, o->stream);
       SHF_CUDA(g, cudaGetLastError());
-      SHF_CUDA(g, cudaMemcpyAsync(dst[f], o->d_stage, count * sizeof(double), cudaMemcpyDeviceToHost, o->stream));
+      SHF_CUDA(g, cudaMemcpyAsync(dst[f], o->d_stage + f * count, count * sizeof(double), cudaMemcpyDeviceToHost,
+                                  o->stream));
     }
-    SHF_CUDA(g, cudaStreamSynchronize(o->stream));
   }
   SHF_CUDA(g, cudaStreamSynchronize(o->stream));
   return SHF_OK;
@@ -955,6 +965,43 @@ int shf_set_fields(shf_grid* g, const double* phi, const double* psi, const doub
   SHF_CUDA(g, cudaSetDevice(owner(g)->device));
   return g->precision == SHF_FP64 ? set_fields_t<double>(g, phi, psi, omega)
                                   : set_fields_t<float>(g, phi, psi, omega);
+}
+
+int shf_set_fields_f32(shf_grid* g, const float* phi, const float* psi, const float* omega) {
+  if (!g || !phi) return fail(g, SHF_EINVAL, "phi must not be NULL");
+  if (g->kind == 1) return fail(g, SHF_EINVAL, "use a member view to set fields of an ensemble");
+  if (g->precision != SHF_FP32) return fail(g, SHF_EINVAL, "float fields need an FP32 grid");
+  shf_grid* o = owner(g);
+  SHF_CUDA(g, cudaSetDevice(o->device));
+  Member& m = *member_of(g);
+  const size_t bytes = (size_t)m.nx * m.ny * sizeof(float);
+  const float* src[3] = {phi, psi, m.rho > 0 ? omega : nullptr};
+  void* dst[3] = {m.phi, m.psi, m.omega};
+  for (int f = 0; f < 3; ++f) {
+    if (src[f]) SHF_CUDA(g, cudaMemcpyAsync(dst[f], src[f], bytes, cudaMemcpyHostToDevice, o->stream));
+    else SHF_CUDA(g, cudaMemsetAsync(dst[f], 0, bytes, o->stream));
+  }
+  SHF_CUDA(g, cudaStreamSynchronize(o->stream));
+  return SHF_OK;
+}
+
+int shf_get_fields_f32(shf_grid* g, float* phi, float* psi, float* omega) {
+  if (!g) return SHF_EINVAL;
+  if (g->kind == 1) return fail(g, SHF_EINVAL, "use a member view to read fields of an ensemble");
+  if (g->precision != SHF_FP32) return fail(g, SHF_EINVAL, "float fields need an FP32 grid");
+  shf_grid* o = owner(g);
+  SHF_CUDA(g, cudaSetDevice(o->device));
+  Member& m = *member_of(g);
+  const size_t count = (size_t)m.nx * m.ny;
+  float* dst[3] = {phi, psi, omega};
+  const void* src[3] = {m.phi, m.psi, m.omega};
+  for (int f = 0; f < 3; ++f) {
+    if (!dst[f]) continue;
+    if (f == 2 && m.rho == 0.0) std::memset(dst[f], 0, count * sizeof(float));
+    else SHF_CUDA(g, cudaMemcpyAsync(dst[f], src[f], count * sizeof(float), cudaMemcpyDeviceToHost, o->stream));
+  }
+  SHF_CUDA(g, cudaStreamSynchronize(o->stream));
+  return SHF_OK;
 }
 
 int shf_init_noise(shf_grid* g, uint64_t seed, double amp) {

@@ -420,6 +420,29 @@ def test_autotune_ensemble_per_size_class():
     ens.close()
 
 
+def test_float_host_fields_round_trip_and_match_double_path():
+    nx, ny = 128, 64
+    p = oracle.Params(rho=1.0, gdot=0.02, dt=0.005)
+    fields = inputs.quench_state(nx, ny, 12, 0.2)
+    f32 = tuple(np.asarray(f, dtype=np.float32) for f in fields)
+    with shf.Grid(nx, ny, 1.0, FP32) as a, shf.Grid(nx, ny, 1.0, FP32) as b:
+        for g in (a, b):
+            g.set_params(p.a, p.b, p.kappa, p.M, p.eta, p.rho, p.gdot, p.dt)
+        a.set_fields_f32(*f32)
+        b.set_fields(*fields)                           # doubles, rounded to float on the device
+        got_a = a.get_fields_f32()
+        for x, y in zip(got_a, f32):
+            assert np.array_equal(x, y)
+        a.step(10)
+        b.step(10)
+        for x, y in zip(a.get_fields_f32(), b.get_fields()):
+            assert np.array_equal(x.astype(np.float64), y)
+    with shf.Grid(32, 32, 1.0, FP64) as g:
+        with pytest.raises(shf.ShfError) as e:
+            g.set_fields_f32(np.zeros((32, 32), np.float32))
+        assert e.value.code == shf.SHF_EINVAL
+
+
 # --------------------------------------------------------------- diagnostics
 
 @pytest.mark.parametrize("prec,tol", [(FP64, 1e-11), (FP32, 1e-5)])
