@@ -63,3 +63,26 @@ def test_inertialess_shear_domains_span_the_system_along_the_flow():
     assert abs(abs(angle) - 90.0) < 20.0, angle
     assert Lpar > 5 * Lperp, (Lpar, Lperp)
     assert Lpar > 0.5 * nx, Lpar                          # of the order of the system size
+
+
+def test_long_run_domain_size_fp32_within_2_percent_of_fp64():
+    """Config C2 (256^2 inertial, rho = eta = 1, gdot = 0.01, dt = 0.005, seeded
+    +-0.01 quench), 20000 steps (t = 100, one strain wrap at t = 50): L_1 from the
+    first moment of S(k) and the principal lengths of Eq. L_matrix, FP32 against
+    the FP64 path (which matches the FP64 oracle to 1e-10), within 2%."""
+    res = {}
+    for prec in (shf.SHF_FP64, shf.SHF_FP32):
+        with shf.Grid(256, 256, 1.0, prec) as g:
+            g.set_params(a=1, b=1, kappa=1, M=1, eta=1, rho=1, gdot=0.01, dt=0.005)
+            g.init_noise(0, 0.01)
+            rows = []
+            for _ in range(10):
+                g.step(2000)
+                moments, _ = g.structure_factor()
+                _, (Lpar, Lperp) = g.gradient_tensor()
+                rows.append((moments[3], Lpar, Lperp))
+            assert g.get_time()[3] == 1                   # the strain wrapped once
+        res[prec] = np.array(rows)
+    rel = np.abs(res[shf.SHF_FP32] - res[shf.SHF_FP64]) / res[shf.SHF_FP64]
+    assert rel.max() <= 0.02, rel
+    assert res[shf.SHF_FP64][-1, 0] > 1.3 * res[shf.SHF_FP64][0, 0]   # the domains coarsened
