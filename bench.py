@@ -376,9 +376,8 @@ def main():
     # gdot log-spaced 1e-4..3e-2) through its graph path, 100 steps per replay
     ensemble = None
     if not args.no_ensemble:
-        nxs = [128 * 2 ** (r // 32) for r in range(96)]
-        eparams = [[1.0, 1.0, 1.0, 1.0, 1.0, float(r % 2), 1e-4 * 300.0 ** (r / 95.0), PARAMS["dt"]]
-                   for r in range(96)]
+        from paper_0710_5912_gb300 import configs
+        nxs, eparams = configs.ensemble_spec(96, PARAMS["dt"])
         ens = shf.Ensemble(nxs, nxs, eparams, seeds=list(range(96)), amp=AMP, precision=shf.SHF_FP32,
                            stream=stream)
         ens.step(100)                                   # warm-up (captures the graph)

@@ -86,3 +86,18 @@ def test_long_run_domain_size_fp32_within_2_percent_of_fp64():
     rel = np.abs(res[shf.SHF_FP32] - res[shf.SHF_FP64]) / res[shf.SHF_FP64]
     assert rel.max() <= 0.02, rel
     assert res[shf.SHF_FP64][-1, 0] > 1.3 * res[shf.SHF_FP64][0, 0]   # the domains coarsened
+
+
+def test_configs_and_logged_run(tmp_path):
+    import json
+    from paper_0710_5912_gb300 import configs, monitor
+    g = configs.make("c2_inertial_256_fp32", gdot=0.01)
+    rows = monitor.run_logged(g, 400, 200, tmp_path / "log.jsonl")
+    g.close()
+    lines = [json.loads(l) for l in open(tmp_path / "log.jsonl")]
+    assert lines == rows and [r["n"] for r in rows] == [200, 400]
+    assert all(abs(r["mean_phi"] - rows[0]["mean_phi"]) < 1e-6 for r in rows)
+    assert rows[-1]["L1"] > 0 and rows[-1]["pts_per_s"] > 0
+    ens = configs.make("c4_ensemble_fp32")
+    assert len(ens.members) == 96
+    ens.close()
