@@ -410,7 +410,8 @@ def main():
                 "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, **PARAMS, "seed": SEED, "amp": AMP,
                            "parallelism": f"replicas x{world}" if world > 1 else "single grid",
                            "l2": "state + scratch 576 MiB > L2 (129 MB): inputs larger than L2, no flush",
-                           "autotuned": {"rowfwd_points": tuned[0][0], "stencil_rows": tuned[0][1]}},
+                           "autotuned": {"rowfwd_phi_points": tuned[0][0], "rowfwd_g_points": tuned[0][1],
+                                         "stencil_rows": tuned[0][2]}},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e,
                 # eight step kernels per step plus the one state-seeding launch of the run
                 "gpu_launches": len(KERNEL_REALS_PER_POINT) * args.steps + 1,

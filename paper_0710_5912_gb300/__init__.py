@@ -192,12 +192,13 @@ def shf_get_fields_f32(h, nx, ny):
 
 
 def shf_autotune(h, cache_path=None, nclasses=8):
-    """Tune the launch variants per size class; returns [(rowfwd_points, stencil_rows), ...]."""
-    out = (ctypes.c_int * (2 * nclasses))()
+    """Tune the launch variants per size class; returns
+    [(rowfwd_phi_points, rowfwd_g_points, stencil_rows), ...]."""
+    out = (ctypes.c_int * (3 * nclasses))()
     path = None if cache_path is None else str(cache_path).encode()
-    _check(lib().shf_autotune(h, path, out, 2 * nclasses), h, "shf_autotune")
-    pairs = [(out[2 * c], out[2 * c + 1]) for c in range(nclasses)]
-    return [p for p in pairs if p[0] > 0]
+    _check(lib().shf_autotune(h, path, out, 3 * nclasses), h, "shf_autotune")
+    triples = [(out[3 * c], out[3 * c + 1], out[3 * c + 2]) for c in range(nclasses)]
+    return [t for t in triples if t[0] > 0]
 
 
 def shf_structure_factor(h, nbins=0):

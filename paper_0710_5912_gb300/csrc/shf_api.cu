@@ -194,16 +194,18 @@ LaunchCfg persistent_cfg(int kind, int nfft, int max_inst, int items, size_t ins
 }
 
 // The tuning knobs of a size class: points per thread of the forward row
-// transforms (8 or 16; FP64: 8) and the stencil tile height (16 or 32, at
-// most ny).  Zero means "the default".
+// transforms of phi and of g (8 or 16 each; FP64: 8) and the stencil tile
+// height (16 or 32, at most ny).  Zero means "the default".
 struct Tune {
-  int rowfwd_points = 0;
+  int rowfwd_phi_points = 0;
+  int rowfwd_g_points = 0;
   int stencil_rows = 0;
 };
 
 template <class T>
 Tune resolved(const SizeClass& cl, Tune t) {
-  if (t.rowfwd_points == 0 || sizeof(T) == 8) t.rowfwd_points = rowfwd_default_points<T>();
+  if (t.rowfwd_phi_points == 0 || sizeof(T) == 8) t.rowfwd_phi_points = rowfwd_default_points<T>();
+  if (t.rowfwd_g_points == 0 || sizeof(T) == 8) t.rowfwd_g_points = rowfwd_default_points<T>();
   const int maxrows = cl.ny < 32 ? cl.ny : 32;
   if (t.stencil_rows == 0 || t.stencil_rows > maxrows) t.stencil_rows = maxrows;
   return t;
@@ -225,10 +227,10 @@ void configure_class_t(SizeClass& cl, Tune tune) {
   cl.cfg[KIND_STENCIL1] = st;
   st.smem = stencil2_smem_bytes(TX, TY, R);
   cl.cfg[KIND_STENCIL2] = st;
-  const int P = tune.rowfwd_points;
-  cl.cfg[KIND_ROWFWD_PHI] =
-      persistent_cfg<T>(KIND_ROWFWD_PHI, nx, ny / 2, 3 * (ny / 2), rowfwd_inst_bytes(nx, R), nmem, P);
-  cl.cfg[KIND_ROWFWD_G] = persistent_cfg<T>(KIND_ROWFWD_G, nx, ny / 2, ny / 2, rowfwd_inst_bytes(nx, R), nmem, P);
+  cl.cfg[KIND_ROWFWD_PHI] = persistent_cfg<T>(KIND_ROWFWD_PHI, nx, ny / 2, 3 * (ny / 2), rowfwd_inst_bytes(nx, R),
+                                               nmem, tune.rowfwd_phi_points);
+  cl.cfg[KIND_ROWFWD_G] = persistent_cfg<T>(KIND_ROWFWD_G, nx, ny / 2, ny / 2, rowfwd_inst_bytes(nx, R), nmem,
+                                             tune.rowfwd_g_points);
   // column items: whole 16-byte chunks (two modes in FP32, one in FP64)
   const int ncol_items = R == 4 ? nx / 4 : nx / 2;
   cl.cfg[KIND_COLPASS_PHI] =
@@ -696,7 +698,7 @@ std::string tune_key(const shf_grid* o, const SizeClass& cl) {
 }
 
 // cache file: a JSON object, one entry per line:
-//   "NXxNY:fp32:inertial": {"rowfwd_points": 16, "stencil_rows": 32},
+//   "NXxNY:fp32:inertial": {"rowfwd_phi_points": 16, "rowfwd_g_points": 8, "stencil_rows": 32},
 std::map<std::string, Tune> read_tune_cache(const char* path) {
   std::map<std::string, Tune> m;
   if (!path) return m;
@@ -706,8 +708,8 @@ std::map<std::string, Tune> read_tune_cache(const char* path) {
   while (std::fgets(line, sizeof(line), f)) {
     char key[256];
     Tune t;
-    if (std::sscanf(line, " \"%255[^\"]\": {\"rowfwd_points\": %d, \"stencil_rows\": %d", key, &t.rowfwd_points,
-                    &t.stencil_rows) == 3)
+    if (std::sscanf(line, " \"%255[^\"]\": {\"rowfwd_phi_points\": %d, \"rowfwd_g_points\": %d, \"stencil_rows\": %d",
+                    key, &t.rowfwd_phi_points, &t.rowfwd_g_points, &t.stencil_rows) == 4)
       m[key] = t;
   }
   std::fclose(f);
@@ -720,8 +722,9 @@ bool write_tune_cache(const char* path, const std::map<std::string, Tune>& m) {
   std::fprintf(f, "{\n");
   size_t i = 0;
   for (const auto& kv : m) {
-    std::fprintf(f, "  \"%s\": {\"rowfwd_points\": %d, \"stencil_rows\": %d}%s\n", kv.first.c_str(),
-                 kv.second.rowfwd_points, kv.second.stencil_rows, ++i < m.size() ? "," : "");
+    std::fprintf(f, "  \"%s\": {\"rowfwd_phi_points\": %d, \"rowfwd_g_points\": %d, \"stencil_rows\": %d}%s\n",
+                 kv.first.c_str(), kv.second.rowfwd_phi_points, kv.second.rowfwd_g_points, kv.second.stencil_rows,
+                 ++i < m.size() ? "," : "");
   }
   std::fprintf(f, "}\n");
   return std::fclose(f) == 0;
@@ -758,18 +761,19 @@ template <class T>
 int tune_class(shf_grid* o, SizeClass& cl, Tune* best) {
   Tune t = resolved<T>(cl, Tune{});
   if (sizeof(T) == 4) {
-    const int fwd[2] = {KIND_ROWFWD_PHI, KIND_ROWFWD_G};
-    float bestms = 0.f;
-    for (int P : {8, 16}) {
-      Tune c = t;
-      c.rowfwd_points = P;
-      configure_class_t<T>(cl, c);
-      float ms = 0.f;
-      const int rc = time_kinds<T>(o, cl, fwd, 2, &ms);
-      if (rc) return rc;
-      if (P == 8 || ms < bestms) {
-        bestms = ms;
-        t.rowfwd_points = P;
+    for (int kind : {KIND_ROWFWD_PHI, KIND_ROWFWD_G}) {   // the two forward passes tuned separately
+      float bestms = 0.f;
+      for (int P : {8, 16}) {
+        Tune c = t;
+        (kind == KIND_ROWFWD_PHI ? c.rowfwd_phi_points : c.rowfwd_g_points) = P;
+        configure_class_t<T>(cl, c);
+        float ms = 0.f;
+        const int rc = time_kinds<T>(o, cl, &kind, 1, &ms);
+        if (rc) return rc;
+        if (P == 8 || ms < bestms) {
+          bestms = ms;
+          (kind == KIND_ROWFWD_PHI ? t.rowfwd_phi_points : t.rowfwd_g_points) = P;
+        }
       }
     }
   }
@@ -1160,9 +1164,10 @@ int shf_autotune(shf_grid* g, const char* cache_path, int* choices, int nchoices
     configure_class(cl, g->precision, t);
     if (g->precision == SHF_FP64) t = resolved<double>(cl, t);
     else t = resolved<float>(cl, t);
-    if ((int)(2 * c + 1) < nchoices) {
-      choices[2 * c] = t.rowfwd_points;
-      choices[2 * c + 1] = t.stencil_rows;
+    if ((int)(3 * c + 2) < nchoices) {
+      choices[3 * c] = t.rowfwd_phi_points;
+      choices[3 * c + 1] = t.rowfwd_g_points;
+      choices[3 * c + 2] = t.stencil_rows;
     }
   }
   if (g->graph) {                                       // re-captured with the new launch shapes
