@@ -1,19 +1,23 @@
-// Block-level complex FFT in shared memory for the row and column passes.
+// Block-level complex FFTs for the row and column passes.
 //
 // The paper's transforms (Appendix B: real <-> reciprocal space "x -> q_x and
 // y -> q_y", done with a CPU library) are done here by a hand-written
 // Stockham auto-sort FFT: every stage reads R values at stride N/R, applies the
 // stage twiddles, performs a radix-R DFT in registers and writes the results to
 // their auto-sorted positions, so the output comes out in natural order with no
-// bit reversal.  Each participating thread holds 8 complex values per buffer;
-// a stage is radix 8 (one butterfly per thread), or radix 4 / radix 2 for the
-// last stage when log2(N) is not a multiple of 3.
+// bit reversal.
+//
+// - fft_reg / fft_reg2 (the step kernels): each thread holds P = 8 (or 16)
+//   complex values in registers; a stage is radix P (one butterfly per
+//   thread), or radix 8 / 4 / 2 for the last stage; stages exchange through a
+//   padded shared buffer.  Twiddles come from per-stage tables (below).
+// - fft_smem (the structure-factor diagnostics): in-place in shared memory,
+//   8 values per thread per stage, twiddles from one table
+//   W[k] = exp(+2 pi i k / NMAX) read with stride NMAX / N.
 //
 // Conventions (shared with the host code): forward uses exp(-2 pi i jk / N),
-// inverse uses exp(+2 pi i jk / N) without scaling.  Twiddles come from one
-// table W[k] = exp(+2 pi i k / NMAX), k < NMAX, computed on the host in double
-// precision and rounded once to the working precision; a length-N transform
-// reads it with stride NMAX / N.
+// inverse uses exp(+2 pi i jk / N) without scaling.  All tables are computed on
+// the host in double precision and rounded once to the working precision.
 #pragma once
 #include <cuda_runtime.h>
 

@@ -7,12 +7,6 @@
 
 namespace shf {
 
-// Per-member descriptor, resident in device memory (one entry per run of a
-// batched launch; blockIdx.y selects the member).  All fields are row-major
-// ny x nx reals; the x-spectral ("row-transformed") buffers hold, per row j,
-// the modes m = 0 .. nx/2-1 of the row's real DFT in a tiled order (see
-// step_kernels.cu); the Nyquist column m = nx/2 is zeroed by the scheme and
-// only the row coefficient of phi* / omega* is kept, to subtract it.
 // Per-member step state in device memory: the step counter n and the strain
 // bookkeeping of the step that starts at n (Section V), evaluated once per
 // step by a single thread (the last kernel of the previous step, or
@@ -23,6 +17,12 @@ struct StepState {
   double s0, s1;    // s(t^n), s(t^{n+1})
 };
 
+// Per-member descriptor, resident in device memory (one entry per run of a
+// batched launch; blockIdx.y selects the member).  All fields are row-major
+// ny x nx reals; the x-spectral ("row-transformed") buffers hold, per row j,
+// the modes m = 0 .. nx/2-1 of the row's real DFT in a tiled order (see
+// step_kernels.cu); the Nyquist column m = nx/2 is zeroed by the scheme and
+// only the row coefficient of phi* / omega* is kept, to subtract it.
 struct MemberDesc {
   void* phi;
   void* psi;

@@ -6,9 +6,9 @@
 //                Eq. p1y stencils): phi* = phi - dt J(psi, phi) and omega* =
 //                omega - dt J(psi, omega), real; omega* is written at the
 //                relabelled positions when the strain wraps during the step.
-//   rowfwd_phi   row (x) transforms of (phi*, f = phi^3) per row and of the
-//                omega* row pair -> x-spectral buffers, plus each row's real
-//                Nyquist coefficient of phi* and omega*.
+//   rowfwd_phi   row (x) transforms of the phi*, f = phi^3 and omega* row
+//                pairs -> x-spectral buffers, plus each row's real Nyquist
+//                coefficient of phi* and omega*.
 //   colpass_phi  column (y) transforms of phi*, f; the Cahn-Hilliard update of
 //                item 1 in the paper's increment form
 //                  phi^{n+1} = phi* + (1 + D4/2)^-1 (-D2 phi* - D4 phi* + D2 f),
@@ -32,12 +32,13 @@
 // This file holds the stencils and the launch dispatch; the transform kernels
 // are in step_rows.cu and step_cols.cu (compiled per transform length).
 //
-// Execution: the stencils run on 2D tiles; the transform kernels are
-// persistent -- every instance walks its work items (row pairs or columns) with
-// a grid stride and, while transforming one item, streams the next item's
-// input into a shared-memory staging buffer with cp.async, so the loads in
-// flight hold shared memory rather than registers.  The FFT itself keeps 8
-// points per thread in registers (fft_block.cuh).
+// Execution: the stencils run on 2D tiles, 4 x 4 outputs per thread; the
+// transform kernels are persistent -- every instance walks its work items (row
+// pairs or column chunks) with a grid stride and, while transforming one item,
+// streams the next item's input into a shared-memory staging buffer with
+// cp.async, so the loads in flight hold shared memory rather than registers.
+// The FFT keeps 8 (or, in the FP32 forward rows, 16) points per thread in
+// registers (fft_block.cuh).
 //
 // Layout: real fields ny x nx row-major.  x-spectral buffers hold, for each row
 // j, the modes m = 0..nx/2-1 of the row's real DFT (the Nyquist column is
