@@ -287,9 +287,12 @@ __device__ __forceinline__ void stencil2_body(const MemberDesc& D, const T* tp, 
   if (tid < NQ * RG) {
     const int k = tid % NQ, rg = tid / NQ;
     const int c = 4 * (k + 1);
-    const int r0 = rg * RPT, r1 = min(r0 + RPT, HM);
+    const int r0 = rg * RPT;
     Six<T> Dn = ld6(tp + r0 * W + c), Cn = ld6(tp + (r0 + 1) * W + c);
-    for (int rm = r0; rm < r1; ++rm) {
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {                     // a fixed trip count, so the window stays in registers
+      const int rm = r0 + i;
+      if (rm >= HM) break;
       const Six<T> Un = ld6(tp + (rm + 2) * W + c);
       T m[4];
 #pragma unroll
