@@ -10,7 +10,8 @@
 // - fft_reg / fft_reg2 (the step kernels): each thread holds P = 8 (or 16)
 //   complex values in registers; a stage is radix P (one butterfly per
 //   thread), or radix 8 / 4 / 2 for the last stage; stages exchange through a
-//   padded shared buffer.  Twiddles come from per-stage tables (below).
+//   padded shared buffer.  Twiddles come from per-stage tables (below), copied
+//   once per CTA into shared memory in a compact per-length form.
 // - fft_smem (the structure-factor diagnostics): in-place in shared memory,
 //   8 values per thread per stage, twiddles from one table
 //   W[k] = exp(+2 pi i k / NMAX) read with stride NMAX / N.
@@ -244,21 +245,47 @@ __host__ __device__ constexpr int stage_table_offset(int a, int LR) {
 // complex entries of the whole table (pairs for a = 0..11, LR = 1..4)
 __host__ __device__ constexpr int stage_table_len() { return 2 * 4 * ((1 << 12) - 1); }
 
-__device__ __forceinline__ void load_pair(const float2* __restrict__ p, float2& w1, float2& w2) {
-  const float4 x = __ldg(reinterpret_cast<const float4*>(p));
+// Compact per-length tables in shared memory.  A register transform with
+// 2^LP points per thread multiplies by twiddles only in its stages a = LP,
+// 2 LP, ... (a = log2 Ns < log2 N; the last one of radix 2^(log2 N - a) <=
+// 2^LP).  The compact table holds the Ns pairs of exactly these stages, in
+// stage order: stage a starts at pair (2^a - 2^LP) / (2^LP - 1), the sum of
+// the earlier stages' 2^b.  Each transform kernel copies it from the global
+// table once per CTA, so the butterflies read their pair from shared memory.
+__host__ __device__ constexpr int compact_stage_offset(int a, int LP) {
+  return a < LP ? 0 : ((1 << a) - (1 << LP)) / ((1 << LP) - 1);
+}
+// pairs of the compact table of an N = 2^log2N transform
+__host__ __device__ constexpr int compact_stage_pairs(int log2N, int LP) {
+  return compact_stage_offset(((log2N - 1) / LP) * LP + LP, LP);
+}
+template <class C>
+__device__ __forceinline__ void stage_tables_to_smem(C* dst, const C* __restrict__ tw, int log2N, int LP, int tid,
+                                                     int nthr) {
+  for (int a = LP; a < log2N; a += LP) {
+    const int LR = log2N - a < LP ? log2N - a : LP;
+    const C* src = tw + 2 * stage_table_offset(a, LR);
+    C* d = dst + 2 * compact_stage_offset(a, LP);
+    for (int i = tid; i < (2 << a); i += nthr) d[i] = __ldg(src + i);
+  }
+}
+
+__device__ __forceinline__ void load_pair(const float2* p, float2& w1, float2& w2) {
+  const float4 x = *reinterpret_cast<const float4*>(p);
   w1 = float2{x.x, x.y};
   w2 = float2{x.z, x.w};
 }
-__device__ __forceinline__ void load_pair(const double2* __restrict__ p, double2& w1, double2& w2) {
-  w1 = __ldg(p);
-  w2 = __ldg(p + 1);
+__device__ __forceinline__ void load_pair(const double2* p, double2& w1, double2& w2) {
+  w1 = p[0];
+  w2 = p[1];
 }
 
-// the R factors W_L^{k r}, r = 0..R-1, of butterfly k of a stage
-template <int R, class C>
-__device__ __forceinline__ void load_stage_factors(const C* __restrict__ tab, int log2Ns, int LR, int k, C (&f)[R]) {
+// the R factors W_L^{k r}, r = 0..R-1, of butterfly k of a stage, from the
+// compact table of a transform with 2^LP points per thread
+template <int R, int LP, class C>
+__device__ __forceinline__ void load_stage_factors(const C* tab, int log2Ns, int k, C (&f)[R]) {
   C w1, w2;
-  load_pair(tab + 2 * (stage_table_offset(log2Ns, LR) + k), w1, w2);
+  load_pair(tab + 2 * (compact_stage_offset(log2Ns, LP) + k), w1, w2);
   f[1] = w1;
   if (R > 2) {
     f[2] = w2;
@@ -291,8 +318,7 @@ __device__ __forceinline__ void dft_radix(C* v) {
 template <int P> constexpr int log2_points() { return P == 16 ? 4 : 3; }
 
 template <bool INV, int LR, bool LAST, int P, class C>
-__device__ __forceinline__ void fft_reg_stage(C (&v)[P], int log2N, int log2Ns, int t, C* buf,
-                                              const C* __restrict__ twt) {
+__device__ __forceinline__ void fft_reg_stage(C (&v)[P], int log2N, int log2Ns, int t, C* buf, const C* twt) {
   constexpr int R = 1 << LR;
   constexpr int B = P >> LR;
   const int T = 1 << (log2N - log2_points<P>());
@@ -306,7 +332,7 @@ __device__ __forceinline__ void fft_reg_stage(C (&v)[P], int log2N, int log2Ns, 
     for (int r = 0; r < R; ++r) w[r] = v[b + r * B];
     if (log2Ns > 0) {
       C f[R];
-      load_stage_factors<R>(twt, log2Ns, LR, k, f);
+      load_stage_factors<R, log2_points<P>()>(twt, log2Ns, k, f);
 #pragma unroll
       for (int r = 1; r < R; ++r) w[r] = cmul(w[r], INV ? f[r] : cconj(f[r]));
     }
@@ -330,10 +356,11 @@ __device__ __forceinline__ void fft_reg_stage(C (&v)[P], int log2N, int log2Ns, 
 
 // Transform of N = 2^log2N points (16 <= N <= NMAX) held as v[q] = x[t + T q].
 // buf: this instance's padded exchange buffer (padded_len(N) elements); tw:
-// the stage tables (stage_table_offset).  All threads of the CTA must call it
-// (barriers) with the same log2N.
+// the compact stage table of this length and P (compact_stage_offset) in
+// shared memory.  All threads of the CTA must call it (barriers) with the same
+// log2N.
 template <bool INV, int P, class C>
-__device__ __forceinline__ void fft_reg(C (&v)[P], int log2N, int t, C* buf, const C* __restrict__ tw) {
+__device__ __forceinline__ void fft_reg(C (&v)[P], int log2N, int t, C* buf, const C* tw) {
   constexpr int LP = log2_points<P>();
   int log2Ns = 0;
   while (log2N - log2Ns > LP) {
@@ -354,7 +381,7 @@ __device__ __forceinline__ void fft_reg(C (&v)[P], int log2N, int t, C* buf, con
 // schedule as fft_reg.
 template <bool INV, int LR, bool LAST>
 __device__ __forceinline__ void fft_reg2_stage(float2 (&a)[kP], float2 (&b)[kP], int log2N, int log2Ns, int t,
-                                               float4* buf, const float2* __restrict__ twt) {
+                                               float4* buf, const float2* twt) {
   using C = float2;
   constexpr int R = 1 << LR;
   constexpr int B = kP >> LR;
@@ -372,7 +399,7 @@ __device__ __forceinline__ void fft_reg2_stage(float2 (&a)[kP], float2 (&b)[kP],
     }
     if (log2Ns > 0) {
       C f[R];
-      load_stage_factors<R>(twt, log2Ns, LR, k, f);
+      load_stage_factors<R, kLogP>(twt, log2Ns, k, f);
 #pragma unroll
       for (int r = 1; r < R; ++r) {
         const C fr = INV ? f[r] : cconj(f[r]);
@@ -408,7 +435,7 @@ __device__ __forceinline__ void fft_reg2_stage(float2 (&a)[kP], float2 (&b)[kP],
 
 template <bool INV>
 __device__ __forceinline__ void fft_reg2(float2 (&a)[kP], float2 (&b)[kP], int log2N, int t, float4* buf,
-                                         const float2* __restrict__ tw) {
+                                         const float2* tw) {
   int log2Ns = 0;
   while (log2N - log2Ns > kLogP) {
     fft_reg2_stage<INV, kLogP, false>(a, b, log2N, log2Ns, t, buf, tw);

@@ -174,17 +174,18 @@ LaunchCfg persistent_cfg(int kind, int nfft, int max_inst, int items, size_t ins
   const bool fwd = kind == KIND_ROWFWD_PHI || kind == KIND_ROWFWD_G;
   const int cta = fwd ? rowfwd_cta_threads(P) : 512;
   const int Tf = nfft / P;
+  int log2n = 0;
+  while ((1 << log2n) < nfft) ++log2n;
+  const size_t tab = stage_table_bytes(log2n, P == 16 ? 4 : 3, sizeof(T));   // shared twiddle table
   int ipc = cta / Tf;
   if (ipc < 1) ipc = 1;
   if (ipc > max_inst) ipc = max_inst;
-  while (ipc > 1 && ipc * inst_bytes > kSmemLimit) ipc /= 2;
+  while (ipc > 1 && ipc * inst_bytes + tab > kSmemLimit) ipc /= 2;
   c.inst_per_cta = ipc;
   c.threads = ipc * Tf;
-  c.smem = ipc * inst_bytes;
+  c.smem = ipc * inst_bytes + tab;
   c.variant = fwd ? P : 0;
   const int work = (items + ipc - 1) / ipc;
-  int log2n = 0;
-  while ((1 << log2n) < nfft) ++log2n;
   const int resident = step_kernel_occupancy<T>(kind, log2n, c.variant, c.threads, c.smem) * sm_count();
   int g = (resident + nmem - 1) / nmem;
   if (g > work) g = work;

@@ -92,6 +92,11 @@ __host__ __device__ constexpr size_t colpass_inst_bytes(int ny, size_t /*real_by
 __host__ __device__ constexpr size_t rowinv_inst_bytes(int nx, size_t real_bytes) {
   return round128(((size_t)nx + (size_t)padded_len(nx)) * 2 * real_bytes);
 }
+// the compact twiddle table that follows the instances of a transform kernel
+// (2^LP points per thread): two complex values per pair
+__host__ __device__ constexpr size_t stage_table_bytes(int log2n, int LP, size_t real_bytes) {
+  return round128((size_t)compact_stage_pairs(log2n, LP) * 4 * real_bytes);
+}
 
 // Forward row transforms come in two variants, P = 8 points per thread
 // (radix-8 stages, 512-thread CTAs) and P = 16 (radix-16 stages, 256-thread

@@ -38,6 +38,12 @@ struct ColConsts {
         ny(ny_), stokes(D.stokes != 0) {}
 };
 
+// Quotients of the flow multipliers: FP32 takes the hardware reciprocal
+// (__fdividef, within 2 ulp; the divisors here lie in [1e-12, 1e3]), FP64 the
+// IEEE quotient.
+__device__ __forceinline__ float flow_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double flow_div(double a, double b) { return a / b; }
+
 // The multiplier at mode (m, row nn) of the column transform, in place:
 // mode 0: va = phi*_hat -> increment of phi_hat (x norm), vb = f_hat;
 // mode 1: va = g_hat -> psi_hat (x norm), vb = omega*_hat -> increment (x norm).
@@ -66,7 +72,7 @@ __device__ __forceinline__ void col_multiply(int mode, const ColConsts<T>& K, in
     const bool zero = nyq_row || (m == 0 && nn == 0);
     const C G = va;
     if (K.stokes) {
-      const T inv = zero ? T(0) : norm / (k2 * k2);
+      const T inv = zero ? T(0) : flow_div(norm, k2 * k2);
       va = C{G.x * inv, G.y * inv};
     } else {
       const C Wv = vb;
@@ -75,9 +81,9 @@ __device__ __forceinline__ void col_multiply(int mode, const ColConsts<T>& K, in
         vb = C{-Wv.x * norm, -Wv.y * norm};             // omega^{n+1} -> 0 there
       } else {
         const T cc = K.cnu * k2;
-        const T inv = T(1) / (T(1) + cc);
+        const T inv = flow_div(T(1), T(1) + cc);
         const C dw = C{(-T(2) * cc * Wv.x + K.dt * G.x) * inv, (-T(2) * cc * Wv.y + K.dt * G.y) * inv};
-        const T ik = norm / k2;
+        const T ik = flow_div(norm, k2);
         va = C{(Wv.x + dw.x) * ik, (Wv.y + dw.y) * ik};
         vb = C{dw.x * norm, dw.y * norm};
       }
@@ -107,6 +113,8 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_colpass(const MemberDesc
   C* buf = st1 + ny;
   C* in0 = static_cast<C*>(mode == 0 ? D.xs_phi : D.xs_g);
   C* in1 = static_cast<C*>(mode == 0 ? D.xs_f : D.xs_w);
+  C* tws = reinterpret_cast<C*>(smem_raw + (size_t)ipc * colpass_inst_bytes(ny, sizeof(T)));
+  stage_tables_to_smem(tws, tw, log2ny, kLogP, threadIdx.x, blockDim.x);
 
   auto issue = [&](int m) {
     if (m < nitems) {
@@ -135,20 +143,20 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_colpass(const MemberDesc
     }
     __syncthreads();                                    // stage free
     issue(m + stride);
-    fft_reg<false>(va, log2ny, t, buf, tw);
-    if (two) fft_reg<false>(vb, log2ny, t, buf, tw);
+    fft_reg<false>(va, log2ny, t, buf, tws);
+    if (two) fft_reg<false>(vb, log2ny, t, buf, tws);
     const double qx_d = mm * K.qx_unit;
     const T qx = (T)qx_d;
     const T sqx = (T)(K.s_d * qx_d);                    // s q_x formed in double
 #pragma unroll
     for (int q = 0; q < kP; ++q) col_multiply<T>(mode, K, mm, qx, sqx, t + q * Tc, va[q], vb[q]);
-    fft_reg<true>(va, log2ny, t, buf, tw);
+    fft_reg<true>(va, log2ny, t, buf, tws);
     if (active) {
 #pragma unroll
       for (int q = 0; q < kP; ++q) in0[xs_idx(t + q * Tc, m, ny, LC)] = va[q];
     }
     if (mode == 1 && !stokes) {
-      fft_reg<true>(vb, log2ny, t, buf, tw);
+      fft_reg<true>(vb, log2ny, t, buf, tws);
       if (active) {
 #pragma unroll
         for (int q = 0; q < kP; ++q) in1[xs_idx(t + q * Tc, m, ny, LC)] = vb[q];
@@ -185,6 +193,8 @@ __global__ void __launch_bounds__(512, 1) k_colpass_pair(const MemberDesc* __res
   float4* buf = st1 + ny;
   float4* in0 = static_cast<float4*>(mode == 0 ? D.xs_phi : D.xs_g);
   float4* in1 = static_cast<float4*>(mode == 0 ? D.xs_f : D.xs_w);
+  float2* tws = reinterpret_cast<float2*>(smem_raw + (size_t)ipc * colpass_inst_bytes(ny, sizeof(T)));
+  stage_tables_to_smem(tws, tw, log2ny, kLogP, threadIdx.x, blockDim.x);
 
   auto issue = [&](int cb) {
     if (cb < nitems) {
@@ -219,8 +229,8 @@ __global__ void __launch_bounds__(512, 1) k_colpass_pair(const MemberDesc* __res
     }
     __syncthreads();                                    // stage free
     issue(cb + stride);
-    fft_reg2<false>(a0, b0, log2ny, t, buf, tw);
-    if (two) fft_reg2<false>(a1, b1, log2ny, t, buf, tw);
+    fft_reg2<false>(a0, b0, log2ny, t, buf, tws);
+    if (two) fft_reg2<false>(a1, b1, log2ny, t, buf, tws);
     const int m0 = active ? 2 * cb : 0, m1 = m0 + 1;
     const double qa_d = m0 * K.qx_unit, qb_d = m1 * K.qx_unit;
     const T qa = (T)qa_d, qb = (T)qb_d;
@@ -230,14 +240,14 @@ __global__ void __launch_bounds__(512, 1) k_colpass_pair(const MemberDesc* __res
       col_multiply<T>(mode, K, m0, qa, sqa, t + q * Tc, a0[q], a1[q]);
       col_multiply<T>(mode, K, m1, qb, sqb, t + q * Tc, b0[q], b1[q]);
     }
-    fft_reg2<true>(a0, b0, log2ny, t, buf, tw);
+    fft_reg2<true>(a0, b0, log2ny, t, buf, tws);
     if (active) {
       float4* o = in0 + (size_t)cb * ny;
 #pragma unroll
       for (int q = 0; q < kP; ++q) o[t + q * Tc] = make_float4(a0[q].x, a0[q].y, b0[q].x, b0[q].y);
     }
     if (mode == 1 && !stokes) {
-      fft_reg2<true>(a1, b1, log2ny, t, buf, tw);
+      fft_reg2<true>(a1, b1, log2ny, t, buf, tws);
       if (active) {
         float4* o = in1 + (size_t)cb * ny;
 #pragma unroll

@@ -33,6 +33,8 @@ __global__ void __launch_bounds__(rowfwd_cta_threads(P), rowfwd_min_ctas<T>(P)) 
   const T* phi = static_cast<const T*>(D.phi);
   const T* oms = static_cast<const T*>(D.omega_star);
   const T* gb = static_cast<const T*>(D.gbuf);
+  C* tws = reinterpret_cast<C*>(smem_raw + (size_t)ipc * rowfwd_inst_bytes(nx, sizeof(T)));
+  stage_tables_to_smem(tws, tw, log2nx, log2_points<P>(), threadIdx.x, blockDim.x);
 
   auto issue = [&](int w) {
     if (w < nitems) {
@@ -73,7 +75,7 @@ __global__ void __launch_bounds__(rowfwd_cta_threads(P), rowfwd_min_ctas<T>(P)) 
     }
     __syncthreads();                                    // stage free
     issue(w + stride);                                  // next item streams in during the transform
-    fft_reg<false>(v, log2nx, t, Z, tw);
+    fft_reg<false>(v, log2nx, t, Z, tws);
     reg_to_smem(v, log2nx, t, Z);
     if (active) {
       if (mode == 1) {
@@ -128,6 +130,8 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_rowinv(const MemberDesc*
   unsigned char* base = smem_raw + (size_t)inst * rowinv_inst_bytes(nx, sizeof(T));
   C* stage = reinterpret_cast<C*>(base);               // chunk cb at stage[2 CL cb]
   C* Z = stage + nx;
+  C* tws = reinterpret_cast<C*>(smem_raw + (size_t)ipc * rowinv_inst_bytes(nx, sizeof(T)));
+  stage_tables_to_smem(tws, tw, log2nx, kLogP, threadIdx.x, blockDim.x);
 
   auto issue = [&](int w) {
     if (w < nitems) {
@@ -189,7 +193,7 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_rowinv(const MemberDesc*
         b1[q] = bs[((size_t)j1 << log2nx) + t + q * Tf];
       }
     }
-    fft_reg<true>(v, log2nx, t, Z, tw);
+    fft_reg<true>(v, log2nx, t, Z, tws);
     if (active) {
       if (kind == 1) {
         T* out = static_cast<T*>(D.psi);
