@@ -226,6 +226,19 @@ void configure_class_t(SizeClass& cl, Tune tune) {
   st.variant = TY;
   st.smem = stencil1_smem_bytes(TX, TY, R);
   cl.cfg[KIND_STENCIL1] = st;
+  if (R == 4 && nx >= 128) {
+    // streamed stage-1 stencil: one CTA per resident slot, each warp a strip of
+    // at least four rows
+    LaunchCfg s1{};
+    s1.grid_x = nx / 128;
+    int gy = stencil1_stream_occupancy() * sm_count() / (s1.grid_x * (nmem > 0 ? nmem : 1));
+    const int gmax = ny / 16 > 1 ? ny / 16 : 1;
+    s1.grid_y = gy < 1 ? 1 : (gy > gmax ? gmax : gy);
+    s1.threads = 128;
+    s1.smem = 0;
+    s1.variant = kStencilStream;
+    cl.cfg[KIND_STENCIL1] = s1;
+  }
   st.smem = stencil2_smem_bytes(TX, TY, R);
   cl.cfg[KIND_STENCIL2] = st;
   cl.cfg[KIND_ROWFWD_PHI] = persistent_cfg<T>(KIND_ROWFWD_PHI, nx, ny / 2, 3 * (ny / 2), rowfwd_inst_bytes(nx, R),

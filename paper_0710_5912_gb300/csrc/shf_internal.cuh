@@ -126,7 +126,11 @@ struct LaunchCfg {
   size_t smem;          // dynamic shared memory bytes
   int inst_per_cta;     // transform instances per CTA (persistent kinds)
   int variant;          // forward rows: points per thread (8, 16); stencils: tile rows (16, 32)
+                        // or kStencilStream (stage 1, FP32, nx >= 128)
 };
+constexpr int kStencilStream = 1;
+// resident CTAs per SM of the streamed stage-1 stencil (128 threads, no shared memory)
+int stencil1_stream_occupancy();
 
 template <class T> void launch_step_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int log2ny,
                                            const cplx<T>* tw, const LaunchCfg& c, cudaStream_t st);

@@ -355,6 +355,142 @@ __global__ void __launch_bounds__(256) k_stencil2(const MemberDesc* __restrict__
   else stencil2_body<false, T, TX, TY>(D, tp, tm, sc, x0, y0, log2nx);
 }
 
+// ------------------------------------------------- streamed stage-1 stencil
+// FP32, nx >= 128: the stage-1 stencil without shared tiles.  A warp owns a
+// 128-column segment (4 columns per lane) and walks a strip of consecutive
+// rows, keeping the rows j - 1, j, j + 1 of each field in registers: each row
+// is one 16-byte load per lane, the x +-2 halo comes from the neighbouring
+// lanes by shuffles (lanes 0 and 31 load theirs), the loads of row j + 2 are
+// issued before row j is computed, and lane 0 asks L2 for the warp's row
+// segments kStreamPrefetch rows ahead (bulk prefetch).  The grid holds exactly
+// the resident CTAs, and the rows are split evenly over the warps, so every
+// warp streams about the same number of rows in one wave.  Same arithmetic,
+// in the same order, as k_stencil1.
+constexpr int kStreamPrefetch = 4;      // rows of L2 prefetch ahead (measured best of 2..16)
+constexpr int kStreamThreads = 128;     // four warps per CTA
+
+struct RawRow {
+  float4 q;       // this lane's four columns
+  float2 l, r;    // lane 0: the two columns left of the segment; lane 31: the two right of it
+};
+__device__ __forceinline__ RawRow load_raw(const float* rowp, int x, int lane, int mx) {
+  RawRow w;
+  w.q = __ldg(reinterpret_cast<const float4*>(rowp + x));
+  w.l = lane == 0 ? __ldg(reinterpret_cast<const float2*>(rowp + ((x - 2) & mx))) : float2{0.f, 0.f};
+  w.r = lane == 31 ? __ldg(reinterpret_cast<const float2*>(rowp + ((x + 4) & mx))) : float2{0.f, 0.f};
+  return w;
+}
+// columns x - 2 .. x + 5 of a row from the lanes' quads
+__device__ __forceinline__ Row8<float> widen(const RawRow& w, int lane) {
+  const unsigned full = 0xffffffffu;
+  float l0 = __shfl_up_sync(full, w.q.z, 1), l1 = __shfl_up_sync(full, w.q.w, 1);
+  float r0 = __shfl_down_sync(full, w.q.x, 1), r1 = __shfl_down_sync(full, w.q.y, 1);
+  if (lane == 0) {
+    l0 = w.l.x;
+    l1 = w.l.y;
+  }
+  if (lane == 31) {
+    r0 = w.r.x;
+    r1 = w.r.y;
+  }
+  return Row8<float>{{l0, l1, w.q.x, w.q.y, w.q.z, w.q.w, r0, r1}};
+}
+__device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
+
+template <bool NEG, bool STOKES>
+__device__ __forceinline__ void stencil1_stream_body(const MemberDesc& D, const Shear<float>& sc, int x, int y0,
+                                                     int nrows, int log2nx, int my, int lane) {
+  using T = float;
+  const int nx = 1 << log2nx, mx = nx - 1;
+  const bool wrap = D.remap && sc.dK != 0;
+  const T dt = (T)D.dt, inv2h = (T)D.inv_2h;
+  const T* ph = static_cast<const T*>(D.phi);
+  const T* ps = static_cast<const T*>(D.psi);
+  const T* om = static_cast<const T*>(D.omega);
+  T* phis = static_cast<T*>(D.phi_star);
+  T* oms = static_cast<T*>(D.omega_star);
+  auto rp = [&](const T* f, int y) { return f + ((size_t)(y & my) << log2nx); };
+  Row8<T> pD = widen(load_raw(rp(ph, y0 - 1), x, lane, mx), lane), pC = widen(load_raw(rp(ph, y0), x, lane, mx), lane);
+  Row8<T> sD = widen(load_raw(rp(ps, y0 - 1), x, lane, mx), lane), sC = widen(load_raw(rp(ps, y0), x, lane, mx), lane);
+  Row8<T> oD, oC;
+  if (!STOKES) {
+    oD = widen(load_raw(rp(om, y0 - 1), x, lane, mx), lane);
+    oC = widen(load_raw(rp(om, y0), x, lane, mx), lane);
+  }
+  RawRow pN = load_raw(rp(ph, y0 + 1), x, lane, mx), sN = load_raw(rp(ps, y0 + 1), x, lane, mx), oN;
+  if (!STOKES) oN = load_raw(rp(om, y0 + 1), x, lane, mx);
+#pragma unroll 2
+  for (int j = 0; j < nrows; ++j) {
+    const int y = y0 + j;
+    if (lane == 0) {                                    // the warp's 512-byte segments, rows ahead
+      l2_prefetch(rp(ph, y + kStreamPrefetch) + x, 512);
+      l2_prefetch(rp(ps, y + kStreamPrefetch) + x, 512);
+      if (!STOKES) l2_prefetch(rp(om, y + kStreamPrefetch) + x, 512);
+    }
+    const Row8<T> pU = widen(pN, lane), sU = widen(sN, lane);
+    Row8<T> oU;
+    if (!STOKES) oU = widen(oN, lane);
+    if (j + 1 < nrows) {                                // row y + 2 in flight while row y is computed
+      pN = load_raw(rp(ph, y + 2), x, lane, mx);
+      sN = load_raw(rp(ps, y + 2), x, lane, mx);
+      if (!STOKES) oN = load_raw(rp(om, y + 2), x, lane, mx);
+    }
+    T dxp[4], dyp[4];
+    grad4<NEG>(sU, sC, sD, sc.w0, sc.w1, inv2h, dxp, dyp);
+    {
+      T dxf[4], dyf[4];
+      grad4<NEG>(pU, pC, pD, sc.w0, sc.w1, inv2h, dxf, dyf);
+      T r[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) r[p] = pC.v[p + 2] - dt * (dyp[p] * dxf[p] - dxp[p] * dyf[p]);
+      st4(phis + ((size_t)y << log2nx) + x, r[0], r[1], r[2], r[3]);
+    }
+    if (!STOKES) {
+      T dxf[4], dyf[4];
+      grad4<NEG>(oU, oC, oD, sc.w0, sc.w1, inv2h, dxf, dyf);
+      T r[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) r[p] = oC.v[p + 2] - dt * (dyp[p] * dxf[p] - dxp[p] * dyf[p]);
+      T* orow = oms + ((size_t)y << log2nx);
+      if (!wrap) {
+        st4(orow + x, r[0], r[1], r[2], r[3]);
+      } else {
+        const int sh_y = remap_shift(sc.dK, D.ratio, y, nx);
+#pragma unroll
+        for (int p = 0; p < 4; ++p) orow[(x + p + sh_y) & mx] = r[p];
+      }
+      oD = oC;
+      oC = oU;
+    }
+    pD = pC;
+    pC = pU;
+    sD = sC;
+    sC = sU;
+  }
+}
+
+// grid (nx / 128, G, members); warp w of CTA (bx, by) streams strip
+// s = 4 by + w of the 4 G equal strips of rows
+__global__ void __launch_bounds__(kStreamThreads, 4) k_stencil1_stream(const MemberDesc* __restrict__ descs,
+                                                                       int log2nx, int log2ny) {
+  const MemberDesc& D = descs[blockIdx.z];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int ny = 1 << log2ny, my = ny - 1;
+  const int x = blockIdx.x * 128 + 4 * lane;
+  const int S = gridDim.y * (kStreamThreads / 32), s = blockIdx.y * (kStreamThreads / 32) + w;
+  const int y0 = (int)(((long long)s * ny) / S), y1 = (int)(((long long)(s + 1) * ny) / S);
+  const Shear<float> sc(*D.st, false);                  // s^n
+  if (D.stokes) {
+    if (sc.d > 0) stencil1_stream_body<true, true>(D, sc, x, y0, y1 - y0, log2nx, my, lane);
+    else stencil1_stream_body<false, true>(D, sc, x, y0, y1 - y0, log2nx, my, lane);
+  } else {
+    if (sc.d > 0) stencil1_stream_body<true, false>(D, sc, x, y0, y1 - y0, log2nx, my, lane);
+    else stencil1_stream_body<false, false>(D, sc, x, y0, y1 - y0, log2nx, my, lane);
+  }
+}
+
 // ----------------------------------------------------------------- launchers
 void launch_step_state_init(const MemberDesc* d, int nmem, cudaStream_t st) {
   k_step_state_init<<<(nmem + 127) / 128, 128, 0, st>>>(d, nmem);
@@ -391,10 +527,17 @@ void launch_stencil_ty(int which, const MemberDesc* d, int nmem, int log2nx, int
     default: launch_stencil_t<T, 128, TY>(which, d, nmem, log2nx, log2ny, c, st); break;
   }
 }
-// the tile height TY (16 or 32, at most ny) is the launch's variant
+// the tile height TY (16 or 32, at most ny) is the launch's variant; variant
+// kStencilStream selects the streamed FP32 stage-1 stencil
 template <class T>
 void launch_stencil(int which, const MemberDesc* d, int nmem, int log2nx, int log2ny, const LaunchCfg& c,
                     cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (which == 0 && c.variant == kStencilStream) {
+      k_stencil1_stream<<<dim3(c.grid_x, c.grid_y, nmem), c.threads, 0, st>>>(d, log2nx, log2ny);
+      return;
+    }
+  }
   if (c.variant == 32) launch_stencil_ty<T, 32>(which, d, nmem, log2nx, log2ny, c, st);
   else launch_stencil_ty<T, 16>(which, d, nmem, log2nx, log2ny, c, st);
 }
@@ -417,6 +560,12 @@ template <class T>
 int step_kernel_occupancy(int kind, int log2n, int variant, int threads, size_t smem) {
   if (kind == KIND_COLPASS_PHI || kind == KIND_COLPASS_FLOW) return col_kernel_occupancy<T>(log2n, threads, smem);
   return row_kernel_occupancy<T>(kind, log2n, variant, threads, smem);
+}
+
+int stencil1_stream_occupancy() {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_stencil1_stream, kStreamThreads, 0) != cudaSuccess) nb = 1;
+  return nb < 1 ? 1 : nb;
 }
 
 template <class T>
