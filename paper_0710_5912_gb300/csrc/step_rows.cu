@@ -101,6 +101,14 @@ __global__ void __launch_bounds__(rowfwd_cta_threads(P), rowfwd_min_ctas<T>(P)) 
   cp_async_wait_all();
 }
 
+// one 16-byte shared-memory word as complex values (two floats pairs, or one double pair)
+__device__ __forceinline__ void load16(const float2* p, float2 (&v)[2]) {
+  const float4 x = *reinterpret_cast<const float4*>(p);
+  v[0] = float2{x.x, x.y};
+  v[1] = float2{x.z, x.w};
+}
+__device__ __forceinline__ void load16(const double2* p, double2 (&v)[1]) { v[0] = *p; }
+
 // ====================================================== inverse row transforms
 // Work items: mode 0 (phi): row pairs of the phi increment; mode 1 (flow): per
 // row pair, item 0 = psi, item 1 = the omega increment (inertial members).  The
@@ -128,7 +136,9 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_rowinv(const MemberDesc*
   const int stride = gridDim.x * ipc;
   const int nchunk = (nx >> 1) >> LC;
   unsigned char* base = smem_raw + (size_t)inst * rowinv_inst_bytes(nx, sizeof(T));
-  C* stage = reinterpret_cast<C*>(base);               // chunk cb at stage[2 CL cb]
+  // staged chunks: row j0's chunk cb at stage[CL cb], row j1's at stage[CL (nchunk + cb)],
+  // so that consecutive threads touch consecutive 16-byte words
+  C* stage = reinterpret_cast<C*>(base);
   C* Z = stage + nx;
   C* tws = reinterpret_cast<C*>(smem_raw + (size_t)ipc * rowinv_inst_bytes(nx, sizeof(T)));
   stage_tables_to_smem(tws, tw, log2nx, kLogP, threadIdx.x, blockDim.x);
@@ -140,8 +150,8 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_rowinv(const MemberDesc*
       const int j0 = 2 * (w / nsub);
       for (int cb = t; cb < nchunk; cb += Tf) {
         const C* g = src + ((((size_t)cb * ny) + j0) << LC);
-        cp_async16(stage + 2 * CL * cb, g);
-        cp_async16(stage + 2 * CL * cb + H, g + H);
+        cp_async16(stage + CL * cb, g);
+        cp_async16(stage + CL * (nchunk + cb), g + H);
       }
     }
     cp_async_commit();
@@ -165,10 +175,13 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_rowinv(const MemberDesc*
     cp_async_wait_all();
     __syncthreads();
     for (int cb = t; cb < nchunk; cb += Tf) {
+      C Av[CL], Bv[CL];
+      load16(stage + CL * cb, Av);
+      load16(stage + CL * (nchunk + cb), Bv);
 #pragma unroll
       for (int c = 0; c < CL; ++c) {
         const int k = (cb << LC) + c;
-        const C A = stage[2 * CL * cb + c], B = stage[2 * CL * cb + CL + c];
+        const C A = Av[c], B = Bv[c];
         if (k == 0) {
           Z[pad16(0)] = C{A.x, B.x};
           Z[pad16(nx >> 1)] = zn;
