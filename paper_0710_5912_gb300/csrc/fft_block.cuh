@@ -230,6 +230,10 @@ constexpr int kLogP = 3;
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 // elements of a padded exchange buffer for an N-point transform
 __host__ __device__ constexpr int padded_len(int N) { return N + N / 16; }
+// 16-byte elements (the paired exchange) are padded by one per 8: a quarter
+// warp's scatter at stride 8 then lands in 8 distinct 16-byte bank groups
+__device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
+__host__ __device__ constexpr int padded_len8(int N) { return N + N / 8; }
 
 // Per-stage twiddle tables.  A stage of radix R = 2^LR after sub-transforms of
 // length Ns = 2^a multiplies input r of butterfly k = j mod Ns by W_L^{k r},
@@ -377,7 +381,7 @@ __device__ __forceinline__ void fft_reg(C (&v)[P], int log2N, int t, C* buf, con
 
 // Two transforms of the same length in lock step (FP32): a[] and b[] share
 // every twiddle factor, and each exchange moves both as one 16-byte vector
-// per position (buf: padded_len(N) float4).  Same register layout and stage
+// per position (buf: padded_len8(N) float4, padded by pad8).  Same register layout and stage
 // schedule as fft_reg.
 template <bool INV, int LR, bool LAST>
 __device__ __forceinline__ void fft_reg2_stage(float2 (&a)[kP], float2 (&b)[kP], int log2N, int log2Ns, int t,
@@ -418,14 +422,14 @@ __device__ __forceinline__ void fft_reg2_stage(float2 (&a)[kP], float2 (&b)[kP],
     } else {
       const int base = ((j - k) << LR) + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[pad16(base + r * Ns)] = make_float4(wa[r].x, wa[r].y, wb[r].x, wb[r].y);
+      for (int r = 0; r < R; ++r) buf[pad8(base + r * Ns)] = make_float4(wa[r].x, wa[r].y, wb[r].x, wb[r].y);
     }
   }
   if (!LAST) {
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < kP; ++q) {
-      const float4 x = buf[pad16(t + q * T)];
+      const float4 x = buf[pad8(t + q * T)];
       a[q] = C{x.x, x.y};
       b[q] = C{x.z, x.w};
     }

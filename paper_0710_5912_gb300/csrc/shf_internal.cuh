@@ -85,9 +85,10 @@ __host__ __device__ constexpr size_t rowfwd_inst_bytes(int nx, size_t real_bytes
 }
 // colpass stages two 16-byte-per-row columns (one x-spectral chunk of each
 // input field: 2 complex floats or 1 complex double per row) plus a 16-byte
-// exchange buffer, in both precisions
+// exchange buffer (sized for the pad8 layout of the paired FP32 exchange), in
+// both precisions
 __host__ __device__ constexpr size_t colpass_inst_bytes(int ny, size_t /*real_bytes*/) {
-  return round128((2 * (size_t)ny + (size_t)padded_len(ny)) * 16);
+  return round128((2 * (size_t)ny + (size_t)padded_len8(ny)) * 16);
 }
 __host__ __device__ constexpr size_t rowinv_inst_bytes(int nx, size_t real_bytes) {
   return round128(((size_t)nx + (size_t)padded_len(nx)) * 2 * real_bytes);
