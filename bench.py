@@ -318,9 +318,10 @@ def main():
                for k, v in kernel_ms.items()}
 
     # end to end through the public API with host buffers (pinned), every step:
-    # H2D of phi, psi, omega + step + D2H of the new phi, psi, omega.  The grid
-    # computes in FP32, so the host arrays are float32 (shf_set_fields_f32 /
-    # shf_get_fields_f32, no conversion); the host link runs at ~200 GB/s.
+    # H2D of phi, psi, omega + step + D2H of the new phi, psi, omega, in one
+    # shf_step_host_f32 call (phi's download overlaps the step's flow passes).
+    # The grid computes in FP32, so the host arrays are float32 (no
+    # conversion); the host link runs at ~200 GB/s per direction.
     e2e = None
     if not args.no_e2e:
         host = [torch.empty((NY, NX), dtype=torch.float32, pin_memory=True).numpy() for _ in range(3)]
@@ -332,15 +333,13 @@ def main():
         barrier(world)
         t0 = time.perf_counter()
         for _ in range(E):
-            lib.shf_set_fields_f32(g.handle, ptr[0], ptr[1], ptr[2])
-            lib.shf_step(g.handle, 1)
-            rc = lib.shf_get_fields_f32(g.handle, ptr[0], ptr[1], ptr[2])
+            rc = lib.shf_step_host_f32(g.handle, 1, ptr[0], ptr[1], ptr[2], ptr[0], ptr[1], ptr[2])
             if rc != 0:
-                raise RuntimeError("e2e get_fields failed")
+                raise RuntimeError("e2e shf_step_host_f32 failed")
         t_e2e = allreduce_max(time.perf_counter() - t0, world)
         e2e = {"value": world * NX * NY * E / t_e2e, "unit": UNIT, "steps": E,
                "h2d_bytes_per_step": 3 * 4 * NX * NY, "d2h_bytes_per_step": 3 * 4 * NX * NY,
-               "path": "shf_set_fields_f32 + shf_step(1) + shf_get_fields_f32, float32 pinned host arrays"}
+               "path": "shf_step_host_f32(1 step): upload, step, download; float32 pinned host arrays"}
     g.close()
 
     # same-GPU FP64 path and the FP32 error against it after 200 steps

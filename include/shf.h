@@ -98,6 +98,25 @@ int shf_set_fields(shf_grid* g, const double* phi, const double* psi, const doub
 int shf_set_fields_f32(shf_grid* g, const float* phi, const float* psi, const float* omega);
 int shf_get_fields_f32(shf_grid* g, float* phi, float* psi, float* omega);
 
+/* Host-in, host-out stepping for FP32 single grids: upload the state from
+ * float host arrays, advance nsteps >= 0 steps (Appendix B, as shf_step), and
+ * download the new state, in one synchronising call.
+ *   phi_in, psi_in, omega_in: ny*nx floats each, row-major; phi_in NULL keeps
+ *     the device state (then psi_in and omega_in must be NULL too); psi_in or
+ *     omega_in NULL with phi_in given are taken as zero (omega is ignored for
+ *     Stokes runs), as in shf_set_fields_f32.
+ *   phi_out, psi_out, omega_out: ny*nx floats each, or NULL to skip; omega_out
+ *     of a Stokes run is zero-filled.
+ * The download of phi overlaps the last step's flow passes: phi^{n+1} is final
+ * once the phi row inverse has run (Appendix B item 1), so it is copied on a
+ * second stream while the stage-2 stencil, the g transforms and the flow solve
+ * (items 2-3) still run.  Host arrays in pinned memory move at the link's
+ * full rate; pageable arrays work but are staged by the driver.  Errors:
+ * SHF_EINVAL (ensemble or member view, FP64 grid, inputs without phi_in),
+ * SHF_ESTATE (parameters not set), SHF_ECUDA. */
+int shf_step_host_f32(shf_grid* g, int64_t nsteps, const float* phi_in, const float* psi_in, const float* omega_in,
+                      float* phi_out, float* psi_out, float* omega_out);
+
 /* phi = amp * (2u - 1) per point, u = (z >> 11) * 2^-53 from SplitMix64
  * (Steele, Lea & Flood 2014) started at seed, one draw per point in row-major
  * order; psi = omega = 0 (the quench of Section VII).  Also resets the step

@@ -191,6 +191,23 @@ def shf_get_fields_f32(h, nx, ny):
     return tuple(out)
 
 
+def shf_step_host_f32(h, nx, ny, nsteps, phi=None, psi=None, omega=None, out=None):
+    """Upload (phi, psi, omega) if phi is given, advance nsteps, download into
+    `out` (three float32 (ny, nx) arrays, allocated when None); returns `out`."""
+    arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float32) for a in (phi, psi, omega)]
+    for a in arrs:
+        if a is not None and a.shape != (ny, nx):
+            raise ValueError(f"field shape {a.shape} != ({ny}, {nx})")
+    if out is None:
+        out = tuple(np.empty((ny, nx), dtype=np.float32) for _ in range(3))
+    for a in out:
+        if a is not None and (a.shape != (ny, nx) or a.dtype != np.float32 or not a.flags.c_contiguous):
+            raise ValueError("outputs must be C-contiguous float32 arrays of shape (ny, nx)")
+    _check(lib().shf_step_host_f32(h, int(nsteps), *[_fptr(a) for a in arrs], *[_fptr(a) for a in out]), h,
+           "shf_step_host_f32")
+    return out
+
+
 def shf_autotune(h, cache_path=None, nclasses=8):
     """Tune the launch variants per size class; returns
     [(rowfwd_phi_points, rowfwd_g_points, stencil_rows), ...]."""
@@ -291,6 +308,9 @@ class Grid:
 
     def get_fields_f32(self):
         return shf_get_fields_f32(self.handle, self.nx, self.ny)
+
+    def step_host_f32(self, nsteps, phi=None, psi=None, omega=None, out=None):
+        return shf_step_host_f32(self.handle, self.nx, self.ny, nsteps, phi, psi, omega, out)
 
     def get_time(self):
         return shf_get_time(self.handle)

@@ -124,6 +124,7 @@ SIGNATURES = {
     "shf_set_fields": (c_int, [c_void_p, P_double, P_double, P_double]),
     "shf_set_fields_f32": (c_int, [c_void_p, P_float, P_float, P_float]),
     "shf_get_fields_f32": (c_int, [c_void_p, P_float, P_float, P_float]),
+    "shf_step_host_f32": (c_int, [c_void_p, c_int64, P_float, P_float, P_float, P_float, P_float, P_float]),
     "shf_init_noise": (c_int, [c_void_p, c_uint64, c_double]),
     "shf_bind_device_fields": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "shf_set_step": (c_int, [c_void_p, c_int64]),

@@ -80,6 +80,8 @@ struct shf_grid {
   double* h_pinned = nullptr;
   size_t pinned_count = 0;
   cudaGraphExec_t graph = nullptr;
+  cudaStream_t io_stream = nullptr;   // shf_step_host_f32: the early phi download
+  cudaEvent_t phi_done = nullptr;     // recorded after the last step's phi row inverse
   std::vector<shf_grid*> views;
   std::string err;
 };
@@ -373,6 +375,8 @@ void free_all(shf_grid* g) {
   cudaFree(g->d_stage);
   cudaFree(g->d_scratch);
   if (g->h_pinned) cudaFreeHost(g->h_pinned);
+  if (g->phi_done) cudaEventDestroy(g->phi_done);
+  if (g->io_stream) cudaStreamDestroy(g->io_stream);
   if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
   for (auto* v : g->views) delete v;
   delete g;
@@ -811,6 +815,47 @@ int tune_class(shf_grid* o, SizeClass& cl, Tune* best) {
   return SHF_OK;
 }
 
+// Enqueue nsteps steps on the grid's stream: the state seed, then graph
+// replays of kGraphSteps steps and direct launches for the rest.  With
+// phi_event (a single FP32 grid), the last step is launched directly and
+// phi_event is recorded between its phi passes (after which phi is final) and
+// its flow passes.
+int run_steps(shf_grid* g, long long nsteps, cudaEvent_t phi_event) {
+  if (nsteps > 0) enqueue_state_init(g);
+  const bool split = phi_event && nsteps > 0;
+  long long left = split ? nsteps - 1 : nsteps;
+  if (left >= kGraphSteps) {
+    if (!g->graph) {
+      cudaGraph_t graph;
+      SHF_CUDA(g, cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+      enqueue_steps(g, kGraphSteps);
+      cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
+      if (e != cudaSuccess) return fail(g, SHF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&g->graph, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        g->graph = nullptr;
+        return fail(g, SHF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      }
+    }
+    while (left >= kGraphSteps) {
+      SHF_CUDA(g, cudaGraphLaunch(g->graph, g->stream));
+      left -= kGraphSteps;
+    }
+  }
+  enqueue_steps(g, left);
+  if (split) {
+    for (auto& cl : g->classes)
+      for (int k = 0; k <= KIND_ROWINV_PHI; ++k) launch_kind<float>(g, cl, k);
+    SHF_CUDA(g, cudaEventRecord(phi_event, g->stream));
+    for (auto& cl : g->classes)
+      for (int k = KIND_ROWINV_PHI + 1; k < kKinds; ++k) launch_kind<float>(g, cl, k);
+  }
+  SHF_CUDA(g, cudaGetLastError());
+  g->n += nsteps;
+  return SHF_OK;
+}
+
 }  // namespace
 
 // =========================================================================
@@ -1078,30 +1123,47 @@ int shf_step(shf_grid* g, int64_t nsteps) {
   for (auto& m : g->members)
     if (!m.params_set) return fail(g, SHF_ESTATE, "shf_set_params must be called before shf_step");
   SHF_CUDA(g, cudaSetDevice(g->device));
-  if (nsteps > 0) enqueue_state_init(g);
-  long long left = nsteps;
-  if (left >= kGraphSteps) {
-    if (!g->graph) {
-      cudaGraph_t graph;
-      SHF_CUDA(g, cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
-      enqueue_steps(g, kGraphSteps);
-      cudaError_t e = cudaStreamEndCapture(g->stream, &graph);
-      if (e != cudaSuccess) return fail(g, SHF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-      e = cudaGraphInstantiate(&g->graph, graph, 0);
-      cudaGraphDestroy(graph);
-      if (e != cudaSuccess) {
-        g->graph = nullptr;
-        return fail(g, SHF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
-      }
-    }
-    while (left >= kGraphSteps) {
-      SHF_CUDA(g, cudaGraphLaunch(g->graph, g->stream));
-      left -= kGraphSteps;
+  return run_steps(g, nsteps, nullptr);
+}
+
+int shf_step_host_f32(shf_grid* g, int64_t nsteps, const float* phi_in, const float* psi_in, const float* omega_in,
+                      float* phi_out, float* psi_out, float* omega_out) {
+  if (!g || nsteps < 0) return SHF_EINVAL;
+  if (g->kind != 0) return fail(g, SHF_EINVAL, "shf_step_host_f32 needs a single grid");
+  if (g->precision != SHF_FP32) return fail(g, SHF_EINVAL, "float fields need an FP32 grid");
+  if (!phi_in && (psi_in || omega_in)) return fail(g, SHF_EINVAL, "inputs need phi_in");
+  Member& m = g->members[0];
+  if (!m.params_set) return fail(g, SHF_ESTATE, "shf_set_params must be called before shf_step_host_f32");
+  SHF_CUDA(g, cudaSetDevice(g->device));
+  if (!g->io_stream) SHF_CUDA(g, cudaStreamCreateWithFlags(&g->io_stream, cudaStreamNonBlocking));
+  if (!g->phi_done) SHF_CUDA(g, cudaEventCreateWithFlags(&g->phi_done, cudaEventDisableTiming));
+  const size_t bytes = (size_t)m.nx * m.ny * sizeof(float);
+  if (phi_in) {
+    const float* src[3] = {phi_in, psi_in, m.rho > 0 ? omega_in : nullptr};
+    void* dst[3] = {m.phi, m.psi, m.omega};
+    for (int f = 0; f < 3; ++f) {
+      if (src[f]) SHF_CUDA(g, cudaMemcpyAsync(dst[f], src[f], bytes, cudaMemcpyHostToDevice, g->stream));
+      else SHF_CUDA(g, cudaMemsetAsync(dst[f], 0, bytes, g->stream));
     }
   }
-  enqueue_steps(g, left);
-  SHF_CUDA(g, cudaGetLastError());
-  g->n += nsteps;
+  const bool early = nsteps > 0 && phi_out;
+  const int rc = run_steps(g, nsteps, early ? g->phi_done : nullptr);
+  if (rc) return rc;
+  if (phi_out) {
+    if (early) {                                        // phi is final once the last step's phi passes are done
+      SHF_CUDA(g, cudaStreamWaitEvent(g->io_stream, g->phi_done, 0));
+      SHF_CUDA(g, cudaMemcpyAsync(phi_out, m.phi, bytes, cudaMemcpyDeviceToHost, g->io_stream));
+    } else {
+      SHF_CUDA(g, cudaMemcpyAsync(phi_out, m.phi, bytes, cudaMemcpyDeviceToHost, g->stream));
+    }
+  }
+  if (psi_out) SHF_CUDA(g, cudaMemcpyAsync(psi_out, m.psi, bytes, cudaMemcpyDeviceToHost, g->stream));
+  if (omega_out) {
+    if (m.rho > 0) SHF_CUDA(g, cudaMemcpyAsync(omega_out, m.omega, bytes, cudaMemcpyDeviceToHost, g->stream));
+    else std::memset(omega_out, 0, bytes);
+  }
+  SHF_CUDA(g, cudaStreamSynchronize(g->stream));
+  SHF_CUDA(g, cudaStreamSynchronize(g->io_stream));
   return SHF_OK;
 }
 

@@ -444,6 +444,57 @@ def test_float_host_fields_round_trip_and_match_double_path():
         assert e.value.code == shf.SHF_EINVAL
 
 
+@pytest.mark.parametrize("rho", [1.0, 0.0])
+@pytest.mark.parametrize("nsteps", [0, 1, 3, 101])
+def test_step_host_matches_set_step_get(rho, nsteps):
+    """shf_step_host_f32 (upload, steps, download with phi copied while the
+    flow passes run) gives the same bits as set_fields_f32 + step +
+    get_fields_f32, also across a graph replay (101 steps)."""
+    nx, ny = 128, 64
+    p = oracle.Params(rho=rho, gdot=0.02, dt=0.005)
+    fields = [np.asarray(f, dtype=np.float32) for f in inputs.quench_state(nx, ny, 5, 0.2)]
+    if rho == 0.0:
+        fields[2][:] = 0.0
+    with shf.Grid(nx, ny, 1.0, FP32) as a, shf.Grid(nx, ny, 1.0, FP32) as b:
+        for g in (a, b):
+            g.set_params(p.a, p.b, p.kappa, p.M, p.eta, p.rho, p.gdot, p.dt)
+        out = a.step_host_f32(nsteps, *fields)
+        b.set_fields_f32(*fields)
+        b.step(nsteps)
+        want = b.get_fields_f32()
+        for x, y in zip(out, want):
+            assert np.array_equal(x, y)
+        assert a.get_time()[0] == nsteps
+        # no inputs: continue from the device state; outputs may be skipped
+        phi_only = np.empty((ny, nx), np.float32)
+        a.step_host_f32(2, out=(phi_only, None, None))
+        b.step(2)
+        assert np.array_equal(phi_only, b.get_fields_f32()[0])
+        assert np.array_equal(a.get_fields_f32()[1], b.get_fields_f32()[1])
+
+
+def test_step_host_rejects_bad_calls():
+    with shf.Grid(32, 32, 1.0, FP64) as g:
+        g.set_params(1, 1, 1, 1, 1, 1, 0.01, 0.005)
+        with pytest.raises(shf.ShfError) as e:
+            g.step_host_f32(1, np.zeros((32, 32), np.float32))
+        assert e.value.code == shf.SHF_EINVAL
+    with shf.Grid(32, 32, 1.0, FP32) as g:
+        with pytest.raises(shf.ShfError) as e:
+            g.step_host_f32(1)
+        assert e.value.code == shf.SHF_ESTATE
+        g.set_params(1, 1, 1, 1, 1, 1, 0.01, 0.005)
+        z = np.zeros((32, 32), np.float32)
+        rc = shf.lib().shf_step_host_f32(g.handle, 1, None, z.ctypes.data_as(shf._native.P_float), None,
+                                         None, None, None)
+        assert rc == shf.SHF_EINVAL
+    ens = shf.Ensemble([32, 32], [32, 32], [[1, 1, 1, 1, 1, 1, 0.01, 0.005]] * 2, seeds=[0, 1], amp=0.1,
+                       precision=FP32)
+    rc = shf.lib().shf_step_host_f32(ens.handle, 1, None, None, None, None, None, None)
+    assert rc == shf.SHF_EINVAL
+    ens.close()
+
+
 # --------------------------------------------------------------- diagnostics
 
 @pytest.mark.parametrize("prec,tol", [(FP64, 1e-11), (FP32, 1e-5)])
