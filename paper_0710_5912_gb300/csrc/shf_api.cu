@@ -174,7 +174,8 @@ template <class T>
 LaunchCfg persistent_cfg(int kind, int nfft, int max_inst, int items, size_t inst_bytes, int nmem, int P = kP) {
   LaunchCfg c{};
   const bool fwd = kind == KIND_ROWFWD_PHI || kind == KIND_ROWFWD_G;
-  const int cta = fwd ? rowfwd_cta_threads(P) : 512;
+  const bool rows = fwd || kind == KIND_ROWINV_PHI || kind == KIND_ROWINV_FLOW;
+  const int cta = rows ? rowfwd_cta_threads(P) : 512;
   const int Tf = nfft / P;
   int log2n = 0;
   while ((1 << log2n) < nfft) ++log2n;
@@ -186,7 +187,7 @@ LaunchCfg persistent_cfg(int kind, int nfft, int max_inst, int items, size_t ins
   c.inst_per_cta = ipc;
   c.threads = ipc * Tf;
   c.smem = ipc * inst_bytes + tab;
-  c.variant = fwd ? P : 0;
+  c.variant = rows ? P : 0;
   const int work = (items + ipc - 1) / ipc;
   const int resident = step_kernel_occupancy<T>(kind, log2n, c.variant, c.threads, c.smem) * sm_count();
   int g = (resident + nmem - 1) / nmem;
@@ -253,8 +254,9 @@ void configure_class_t(SizeClass& cl, Tune tune) {
       persistent_cfg<T>(KIND_COLPASS_PHI, ny, ncol_items, ncol_items, colpass_inst_bytes(ny, R), nmem);
   cl.cfg[KIND_COLPASS_FLOW] =
       persistent_cfg<T>(KIND_COLPASS_FLOW, ny, ncol_items, ncol_items, colpass_inst_bytes(ny, R), nmem);
-  cl.cfg[KIND_ROWINV_PHI] = persistent_cfg<T>(KIND_ROWINV_PHI, nx, ny / 2, ny / 2, rowinv_inst_bytes(nx, R), nmem);
-  cl.cfg[KIND_ROWINV_FLOW] = persistent_cfg<T>(KIND_ROWINV_FLOW, nx, ny / 2, ny, rowinv_inst_bytes(nx, R), nmem);
+  const int PI = rowinv_default_points<T>();
+  cl.cfg[KIND_ROWINV_PHI] = persistent_cfg<T>(KIND_ROWINV_PHI, nx, ny / 2, ny / 2, rowinv_inst_bytes(nx, R), nmem, PI);
+  cl.cfg[KIND_ROWINV_FLOW] = persistent_cfg<T>(KIND_ROWINV_FLOW, nx, ny / 2, ny, rowinv_inst_bytes(nx, R), nmem, PI);
   cl.sfrows = sf_row_cfg(nx, ny, nx * Cx);
   cl.sfcols = sf_col_cfg(nx, ny, Cx + 12, Cx);
 }

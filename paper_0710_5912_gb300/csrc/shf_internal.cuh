@@ -99,14 +99,16 @@ __host__ __device__ constexpr size_t stage_table_bytes(int log2n, int LP, size_t
   return round128((size_t)compact_stage_pairs(log2n, LP) * 4 * real_bytes);
 }
 
-// Forward row transforms come in two variants, P = 8 points per thread
-// (radix-8 stages, 512-thread CTAs) and P = 16 (radix-16 stages, 256-thread
-// CTAs, FP32 only); the inverse row and the column passes use 8 points and 512
-// threads.  The default P and the stencil tile height are tuning knobs
-// (shf_autotune).
+// Row transforms come in two variants, P = 8 points per thread (radix-8
+// stages, 512-thread CTAs) and P = 16 (radix-16 stages, 256-thread CTAs, FP32
+// only); the column passes use 8 points and 512 threads.  The forward rows'
+// P and the stencil tile height are tuning knobs (shf_autotune); the FP32
+// inverse rows use P = 16 (8% faster than 8 in the flow pass, equal in the
+// phi pass at 4096^2).
 constexpr int rowfwd_cta_threads(int P) { return P == 16 ? 256 : 512; }
 template <class T> constexpr int rowfwd_min_ctas(int P) { return P == 16 ? 3 : (sizeof(T) == 4 ? 2 : 1); }
 template <class T> constexpr int rowfwd_default_points() { return sizeof(T) == 4 ? 16 : 8; }
+template <class T> constexpr int rowinv_default_points() { return sizeof(T) == 4 ? 16 : 8; }
 
 // The eight launches of a step, in order.
 enum StepKind {

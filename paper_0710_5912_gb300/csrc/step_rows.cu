@@ -116,9 +116,11 @@ __device__ __forceinline__ void load16(const double2* p, double2 (&v)[1]) { v[0]
 // transform; Z[k] = A[k] + i B[k], Z[N-k] = conj A[k] + i conj B[k] (A, B the
 // two rows), Z[0] from the real parts, Z[N/2] = minus the staged field's row
 // Nyquist coefficients / nx.
-template <class T, int LN>
-__global__ void __launch_bounds__(512, min_ctas<T>()) k_rowinv(const MemberDesc* __restrict__ descs, int log2ny,
-                                                               const cplx<T>* __restrict__ tw, int mode) {
+// P = 16 (FP32): 256-thread CTAs, two per SM (128 registers), and the
+// increment bases are loaded after the transform to keep registers free.
+template <class T, int LN, int P>
+__global__ void __launch_bounds__(rowfwd_cta_threads(P), P == 16 ? 2 : min_ctas<T>()) k_rowinv(
+    const MemberDesc* __restrict__ descs, int log2ny, const cplx<T>* __restrict__ tw, int mode) {
   constexpr int log2nx = LN;
   using C = cplx<T>;
   constexpr int LC = Layout<T>::LC;
@@ -127,7 +129,6 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_rowinv(const MemberDesc*
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const MemberDesc& D = descs[blockIdx.y];
   const int nx = 1 << log2nx, ny = 1 << log2ny, mx = nx - 1;
-  constexpr int P = kP;
   const int Tf = nx / P;
   const int ipc = blockDim.x / Tf;
   const int inst = threadIdx.x / Tf, t = threadIdx.x - inst * Tf;
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_rowinv(const MemberDesc*
   C* stage = reinterpret_cast<C*>(base);
   C* Z = stage + nx;
   C* tws = reinterpret_cast<C*>(smem_raw + (size_t)ipc * rowinv_inst_bytes(nx, sizeof(T)));
-  stage_tables_to_smem(tws, tw, log2nx, kLogP, threadIdx.x, blockDim.x);
+  stage_tables_to_smem(tws, tw, log2nx, log2_points<P>(), threadIdx.x, blockDim.x);
 
   auto issue = [&](int w) {
     if (w < nitems) {
@@ -196,17 +197,22 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_rowinv(const MemberDesc*
     C v[P];
     smem_to_reg(v, Z, log2nx, t);
     __syncthreads();                                    // Z becomes the exchange buffer
-    // the real-space base of the increment (phi* or omega*), loaded before the transform
+    // the real-space base of the increment (phi* or omega*): loaded before the
+    // transform with 8 points per thread, after it with 16 (registers)
     T b0[P], b1[P];
-    if (active && kind != 1) {
-      const T* bs = static_cast<const T*>(kind == 0 ? D.phi_star : D.omega_star);
+    auto load_bases = [&]() {
+      if (active && kind != 1) {
+        const T* bs = static_cast<const T*>(kind == 0 ? D.phi_star : D.omega_star);
 #pragma unroll
-      for (int q = 0; q < P; ++q) {
-        b0[q] = bs[((size_t)j0 << log2nx) + t + q * Tf];
-        b1[q] = bs[((size_t)j1 << log2nx) + t + q * Tf];
+        for (int q = 0; q < P; ++q) {
+          b0[q] = bs[((size_t)j0 << log2nx) + t + q * Tf];
+          b1[q] = bs[((size_t)j1 << log2nx) + t + q * Tf];
+        }
       }
-    }
+    };
+    if (P == 8) load_bases();
     fft_reg<true>(v, log2nx, t, Z, tws);
+    if (P == 16) load_bases();
     if (active) {
       if (kind == 1) {
         T* out = static_cast<T*>(D.psi);
@@ -243,6 +249,14 @@ const void* rowfwd_fn(int P) {
   return (const void*)k_rowfwd<T, LN, 8>;
 }
 
+template <class T, int LN>
+const void* rowinv_fn(int P) {
+  if constexpr (sizeof(T) == 4) {
+    if (P == 16) return (const void*)k_rowinv<T, LN, 16>;
+  }
+  return (const void*)k_rowinv<T, LN, 8>;
+}
+
 template <class T>
 void launch_row_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int log2ny, const cplx<T>* tw,
                        const LaunchCfg& c, cudaStream_t st) {
@@ -259,7 +273,13 @@ void launch_row_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int 
       }
       k_rowfwd<T, LN, 8><<<grid, c.threads, c.smem, st>>>(d, log2ny, tw, mode);
     } else {
-      k_rowinv<T, LN><<<grid, c.threads, c.smem, st>>>(d, log2ny, tw, mode);
+      if constexpr (sizeof(T) == 4) {
+        if (c.variant == 16) {
+          k_rowinv<T, LN, 16><<<grid, c.threads, c.smem, st>>>(d, log2ny, tw, mode);
+          return;
+        }
+      }
+      k_rowinv<T, LN, 8><<<grid, c.threads, c.smem, st>>>(d, log2ny, tw, mode);
     }
   });
 }
@@ -270,7 +290,7 @@ int row_kernel_occupancy(int kind, int log2nx, int variant, int threads, size_t 
   with_log2n(log2nx, [&](auto L) {
     constexpr int LN = decltype(L)::value;
     const void* f = (kind == KIND_ROWFWD_PHI || kind == KIND_ROWFWD_G) ? rowfwd_fn<T, LN>(variant)
-                                                                        : (const void*)k_rowinv<T, LN>;
+                                                                        : rowinv_fn<T, LN>(variant);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads, smem) != cudaSuccess) nb = 1;
   });
   return nb < 1 ? 1 : nb;
@@ -283,7 +303,8 @@ void set_row_smem_limits(int lim) {
       constexpr int LN = decltype(L)::value;
       cudaFuncSetAttribute(rowfwd_fn<T, LN>(8), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
       cudaFuncSetAttribute(rowfwd_fn<T, LN>(16), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-      cudaFuncSetAttribute(k_rowinv<T, LN>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      cudaFuncSetAttribute(rowinv_fn<T, LN>(8), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      cudaFuncSetAttribute(rowinv_fn<T, LN>(16), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     });
 }
 
