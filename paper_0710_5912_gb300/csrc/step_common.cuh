@@ -70,6 +70,12 @@ __device__ __forceinline__ void cp_async8(void* s, const void* g) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// ask L2 for `bytes` (a multiple of 16) at p (16-byte aligned): a bulk
+// prefetch issued by one thread, holding no register or shared memory
+__device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // bytes (a multiple of 16, both ends 16-byte aligned) from src to dst
 __device__ __forceinline__ void copy_async(void* dst, const void* src, int bytes, int t, int nthr) {
   char* d = static_cast<char*>(dst);

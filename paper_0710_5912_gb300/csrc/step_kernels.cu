@@ -395,9 +395,6 @@ __device__ __forceinline__ Row8<float> widen(const RawRow& w, int lane) {
   }
   return Row8<float>{{l0, l1, w.q.x, w.q.y, w.q.z, w.q.w, r0, r1}};
 }
-__device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
-}
 
 template <bool NEG, bool STOKES>
 __device__ __forceinline__ void stencil1_stream_body(const MemberDesc& D, const Shear<float>& sc, int x, int y0,

@@ -154,6 +154,12 @@ __global__ void __launch_bounds__(rowfwd_cta_threads(P), P == 16 ? 2 : min_ctas<
         cp_async16(stage + CL * cb, g);
         cp_async16(stage + CL * (nchunk + cb), g + H);
       }
+      // the item's increment bases, read after its transform: into L2 now
+      const bool base = mode == 0 || sub == 1;
+      if (P == 16 && base && t == 0) {
+        const T* bs = static_cast<const T*>(mode == 0 ? D.phi_star : D.omega_star) + ((size_t)j0 << log2nx);
+        l2_prefetch(bs, 2 * nx * (unsigned)sizeof(T));
+      }
     }
     cp_async_commit();
   };
