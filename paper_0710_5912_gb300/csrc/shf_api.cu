@@ -509,7 +509,13 @@ int build(shf_grid* g, const std::vector<int>& nx, const std::vector<int>& ny, c
 template <class T>
 void launch_kind(shf_grid* o, SizeClass& cl, int kind) {
   const cplx<T>* tw = static_cast<const cplx<T>*>(o->d_twr);
-  launch_step_kernel<T>(kind, cl.d_desc, (int)cl.members.size(), cl.log2nx, cl.log2ny, tw, cl.cfg[kind], o->stream);
+  LaunchCfg c = cl.cfg[kind];
+  if (kind == KIND_COLPASS_FLOW) {                      // the flow pass specialised on the members' regime
+    bool inertial = false, stokes = false;
+    for (int r : cl.members) (o->members[r].rho > 0.0 ? inertial : stokes) = true;
+    c.variant = inertial && stokes ? 3 : (stokes ? 2 : 1);
+  }
+  launch_step_kernel<T>(kind, cl.d_desc, (int)cl.members.size(), cl.log2nx, cl.log2ny, tw, c, o->stream);
 }
 
 constexpr int kKinds = KIND_COUNT;
@@ -1019,6 +1025,11 @@ int shf_set_params(shf_grid* g, double a, double b, double kappa, double M, doub
     m.params_set = true;
     rc = upload_desc(o, r);
     if (rc) return fail(g, rc, o->err);
+  }
+  if (o->graph) {                                       // the flow pass kernel depends on the regimes
+    SHF_CUDA(g, cudaStreamSynchronize(o->stream));
+    cudaGraphExecDestroy(o->graph);
+    o->graph = nullptr;
   }
   return SHF_OK;
 }

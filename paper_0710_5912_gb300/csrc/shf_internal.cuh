@@ -128,7 +128,8 @@ struct LaunchCfg {
   int threads;
   size_t smem;          // dynamic shared memory bytes
   int inst_per_cta;     // transform instances per CTA (persistent kinds)
-  int variant;          // forward rows: points per thread (8, 16); stencils: tile rows (16, 32)
+  int variant;          // rows: points per thread (8, 16); stencils: tile rows (16, 32);
+                        // FP32 flow column pass: members' regime (1 inertial, 2 Stokes, 3 mixed)
                         // or kStencilStream (stage 1, FP32, nx >= 128)
 };
 constexpr int kStencilStream = 1;

@@ -44,20 +44,21 @@ struct ColConsts {
 __device__ __forceinline__ float flow_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double flow_div(double a, double b) { return a / b; }
 
-// The multiplier at mode (m, row nn) of the column transform, in place:
-// mode 0: va = phi*_hat -> increment of phi_hat (x norm), vb = f_hat;
-// mode 1: va = g_hat -> psi_hat (x norm), vb = omega*_hat -> increment (x norm).
+// The multiplier at mode (m, row nn) of the column transform, in place, for a
+// compile-time pass kind (0: phi; 1: inertial flow; 2: Stokes flow):
+// kind 0: va = phi*_hat -> increment of phi_hat (x norm), vb = f_hat;
+// kinds 1-2: va = g_hat -> psi_hat (x norm), vb = omega*_hat -> increment (x norm).
 // qx = m q_unit and sqx = s q_x, both formed in double.
-template <class T>
-__device__ __forceinline__ void col_multiply(int mode, const ColConsts<T>& K, int m, T qx, T sqx, int nn,
-                                             cplx<T>& va, cplx<T>& vb) {
+template <int KIND, class T>
+__device__ __forceinline__ void col_multiply_k(const ColConsts<T>& K, int m, T qx, T sqx, int nn, cplx<T>& va,
+                                               cplx<T>& vb) {
   using C = cplx<T>;
   const int ns = nn < (K.ny >> 1) ? nn : nn - K.ny;
   const T ky = (T)ns * K.qyu - sqx;
   const T k2 = qx * qx + ky * ky;
   const bool nyq_row = nn == (K.ny >> 1);
   const T norm = K.norm;
-  if (mode == 0) {
+  if (KIND == 0) {
     const C P = va, F = vb;
     if (nyq_row) {
       va = C{-P.x * norm, -P.y * norm};                 // Nyquist row of phi^{n+1} -> 0
@@ -71,7 +72,7 @@ __device__ __forceinline__ void col_multiply(int mode, const ColConsts<T>& K, in
   } else {
     const bool zero = nyq_row || (m == 0 && nn == 0);
     const C G = va;
-    if (K.stokes) {
+    if (KIND == 2) {
       const T inv = zero ? T(0) : flow_div(norm, k2 * k2);
       va = C{G.x * inv, G.y * inv};
     } else {
@@ -89,6 +90,14 @@ __device__ __forceinline__ void col_multiply(int mode, const ColConsts<T>& K, in
       }
     }
   }
+}
+// the same with the kind chosen at run time (mode 0 or 1, and K.stokes)
+template <class T>
+__device__ __forceinline__ void col_multiply(int mode, const ColConsts<T>& K, int m, T qx, T sqx, int nn,
+                                             cplx<T>& va, cplx<T>& vb) {
+  if (mode == 0) col_multiply_k<0>(K, m, qx, sqx, nn, va, vb);
+  else if (K.stokes) col_multiply_k<2>(K, m, qx, sqx, nn, va, vb);
+  else col_multiply_k<1>(K, m, qx, sqx, nn, va, vb);
 }
 
 template <class T, int LN>
@@ -166,33 +175,27 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_colpass(const MemberDesc
   cp_async_wait_all();
 }
 
-// FP32 column pass over whole chunks: item cb = the two modes m = 2cb, 2cb+1,
-// whose ny rows are one contiguous 16-byte-per-row run in the x-spectral
-// layout.  Both columns are staged with 16-byte copies, transformed in lock
-// step (shared twiddles, 16-byte exchanges) and written back as whole 16-byte
-// rows, so no sector is touched twice.
-template <int LN>
-__global__ void __launch_bounds__(512, 1) k_colpass_pair(const MemberDesc* __restrict__ descs, int log2nx,
-                                                        const float2* __restrict__ tw, int mode) {
+// The FP32 column pass body for one compile-time kind (0: phi; 1: inertial flow; 2:
+// Stokes flow), so no per-point branch on the mode or the member's regime.
+template <int LN, int KIND>
+__device__ __forceinline__ void colpass_pair_body(const MemberDesc& D, int log2nx, const float2* __restrict__ tw,
+                                                  unsigned char* smem_raw) {
   constexpr int log2ny = LN;
+  constexpr bool two = KIND != 2;                       // second input field
   using T = float;
   using C = float2;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const MemberDesc& D = descs[blockIdx.y];
   const int nx = 1 << log2nx, ny = 1 << log2ny;
   const int Tc = ny >> kLogP;
   const int ipc = blockDim.x / Tc;
   const int inst = threadIdx.x / Tc, t = threadIdx.x - inst * Tc;
   const int nitems = nx >> 2;
   const int stride = gridDim.x * ipc;
-  const bool stokes = D.stokes != 0;
-  const bool two = mode == 0 || !stokes;                // second input field
   unsigned char* base = smem_raw + (size_t)inst * colpass_inst_bytes(ny, sizeof(T));
   float4* st0 = reinterpret_cast<float4*>(base);
   float4* st1 = st0 + ny;
   float4* buf = st1 + ny;
-  float4* in0 = static_cast<float4*>(mode == 0 ? D.xs_phi : D.xs_g);
-  float4* in1 = static_cast<float4*>(mode == 0 ? D.xs_f : D.xs_w);
+  float4* in0 = static_cast<float4*>(KIND == 0 ? D.xs_phi : D.xs_g);
+  float4* in1 = static_cast<float4*>(KIND == 0 ? D.xs_f : D.xs_w);
   float2* tws = reinterpret_cast<float2*>(smem_raw + (size_t)ipc * colpass_inst_bytes(ny, sizeof(T)));
   stage_tables_to_smem(tws, tw, log2ny, kLogP, threadIdx.x, blockDim.x);
 
@@ -204,7 +207,7 @@ __global__ void __launch_bounds__(512, 1) k_colpass_pair(const MemberDesc* __res
     cp_async_commit();
   };
 
-  const ColConsts<T> K(D, mode, ny);
+  const ColConsts<T> K(D, KIND == 0 ? 0 : 1, ny);
   const int iters = persistent_iters(nitems, ipc);
   int cb = blockIdx.x * ipc + inst;
   issue(cb);
@@ -237,8 +240,8 @@ __global__ void __launch_bounds__(512, 1) k_colpass_pair(const MemberDesc* __res
     const T sqa = (T)(K.s_d * qa_d), sqb = (T)(K.s_d * qb_d);   // s q_x formed in double
 #pragma unroll
     for (int q = 0; q < kP; ++q) {
-      col_multiply<T>(mode, K, m0, qa, sqa, t + q * Tc, a0[q], a1[q]);
-      col_multiply<T>(mode, K, m1, qb, sqb, t + q * Tc, b0[q], b1[q]);
+      col_multiply_k<KIND>(K, m0, qa, sqa, t + q * Tc, a0[q], a1[q]);
+      col_multiply_k<KIND>(K, m1, qb, sqb, t + q * Tc, b0[q], b1[q]);
     }
     fft_reg2<true>(a0, b0, log2ny, t, buf, tws);
     if (active) {
@@ -246,7 +249,7 @@ __global__ void __launch_bounds__(512, 1) k_colpass_pair(const MemberDesc* __res
 #pragma unroll
       for (int q = 0; q < kP; ++q) o[t + q * Tc] = make_float4(a0[q].x, a0[q].y, b0[q].x, b0[q].y);
     }
-    if (mode == 1 && !stokes) {
+    if (KIND == 1) {
       fft_reg2<true>(a1, b1, log2ny, t, buf, tws);
       if (active) {
         float4* o = in1 + (size_t)cb * ny;
@@ -258,6 +261,34 @@ __global__ void __launch_bounds__(512, 1) k_colpass_pair(const MemberDesc* __res
   cp_async_wait_all();
 }
 
+// FP32 column pass over whole chunks: item cb = the two modes m = 2cb, 2cb+1,
+// whose ny rows are one contiguous 16-byte-per-row run in the x-spectral
+// layout.  Both columns are staged with 16-byte copies, transformed in lock
+// step (shared twiddles, 16-byte exchanges) and written back as whole 16-byte
+// rows, so no sector is touched twice.  The kind is uniform per CTA (one
+// member per blockIdx.y).
+// KIND 0-2 as colpass_pair_body; KIND 3: flow for a launch whose members mix
+// both regimes (the body is chosen per CTA).  One kernel per kind, so each
+// gets its own register allocation.
+template <int LN, int KIND>
+__global__ void __launch_bounds__(512, 1) k_colpass_pair(const MemberDesc* __restrict__ descs, int log2nx,
+                                                        const float2* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const MemberDesc& D = descs[blockIdx.y];
+  if (KIND != 3) colpass_pair_body<LN, KIND>(D, log2nx, tw, smem_raw);
+  else if (D.stokes) colpass_pair_body<LN, 2>(D, log2nx, tw, smem_raw);
+  else colpass_pair_body<LN, 1>(D, log2nx, tw, smem_raw);
+}
+template <int LN>
+const void* colpass_pair_fn(int kind) {
+  switch (kind) {
+    case 0: return (const void*)k_colpass_pair<LN, 0>;
+    case 1: return (const void*)k_colpass_pair<LN, 1>;
+    case 2: return (const void*)k_colpass_pair<LN, 2>;
+    default: return (const void*)k_colpass_pair<LN, 3>;
+  }
+}
+
 // ----------------------------------------------------------------- launchers
 template <class T>
 void launch_col_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int log2ny, const cplx<T>* tw,
@@ -266,9 +297,16 @@ void launch_col_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int 
   const int mode = kind == KIND_COLPASS_PHI ? 0 : 1;
   with_log2n(log2ny, [&](auto L) {
     constexpr int LN = decltype(L)::value;
-    if constexpr (sizeof(T) == 4)
-      k_colpass_pair<LN><<<grid, c.threads, c.smem, st>>>(d, log2nx, tw, mode);
-    else
+    if constexpr (sizeof(T) == 4) {
+      // variant of the flow pass: 1 inertial members, 2 Stokes, 3 mixed
+      const int k = mode == 0 ? 0 : (c.variant >= 1 && c.variant <= 3 ? c.variant : 3);
+      switch (k) {
+        case 0: k_colpass_pair<LN, 0><<<grid, c.threads, c.smem, st>>>(d, log2nx, tw); break;
+        case 1: k_colpass_pair<LN, 1><<<grid, c.threads, c.smem, st>>>(d, log2nx, tw); break;
+        case 2: k_colpass_pair<LN, 2><<<grid, c.threads, c.smem, st>>>(d, log2nx, tw); break;
+        default: k_colpass_pair<LN, 3><<<grid, c.threads, c.smem, st>>>(d, log2nx, tw); break;
+      }
+    } else
       k_colpass<T, LN><<<grid, c.threads, c.smem, st>>>(d, log2nx, tw, mode);
   });
 }
@@ -279,7 +317,7 @@ int col_kernel_occupancy(int log2ny, int threads, size_t smem) {
   with_log2n(log2ny, [&](auto L) {
     constexpr int LN = decltype(L)::value;
     const void* f;
-    if constexpr (sizeof(T) == 4) f = (const void*)k_colpass_pair<LN>;
+    if constexpr (sizeof(T) == 4) f = colpass_pair_fn<LN>(3);
     else f = (const void*)k_colpass<T, LN>;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads, smem) != cudaSuccess) nb = 1;
   });
@@ -291,9 +329,10 @@ void set_col_smem_limits(int lim) {
   for (int ln = 4; ln <= LOG2_NMAX; ++ln)
     with_log2n(ln, [&](auto L) {
       constexpr int LN = decltype(L)::value;
-      if constexpr (sizeof(T) == 4)
-        cudaFuncSetAttribute(k_colpass_pair<LN>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-      else
+      if constexpr (sizeof(T) == 4) {
+        for (int k = 0; k < 4; ++k)
+          cudaFuncSetAttribute(colpass_pair_fn<LN>(k), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      } else
         cudaFuncSetAttribute(k_colpass<T, LN>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     });
 }

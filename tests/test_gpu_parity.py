@@ -473,6 +473,28 @@ def test_step_host_matches_set_step_get(rho, nsteps):
         assert np.array_equal(a.get_fields_f32()[1], b.get_fields_f32()[1])
 
 
+def test_regime_switch_after_graph_capture():
+    """The flow column pass is compiled per regime and chosen on the host, so
+    a CUDA graph captured for an inertial run must not survive set_params to
+    the Stokes regime: 100 graph steps inertial, then 100 Stokes, against the
+    oracle over the same sequence."""
+    nx = ny = 64
+    pi = oracle.Params(rho=1.0, gdot=0.01, dt=0.005)
+    ps = oracle.Params(rho=0.0, gdot=0.01, dt=0.005)
+    fields = rough_state(nx, ny, 21)
+    mid = oracle_run(pi, fields, 0, 100)
+    want = oracle_run(ps, mid, 100, 100)
+    with shf.Grid(nx, ny, 1.0, FP32) as g:
+        g.set_params(pi.a, pi.b, pi.kappa, pi.M, pi.eta, pi.rho, pi.gdot, pi.dt)
+        g.set_fields(*fields)
+        g.step(100)
+        g.set_params(ps.a, ps.b, ps.kappa, ps.M, ps.eta, ps.rho, ps.gdot, ps.dt)
+        g.step(100)
+        got = g.get_fields()
+    assert_close(got, want, 1e-5, 0.0, "inertial then Stokes", FP32,
+                 oracle.strain(200, ps.gdot, ps.dt, nx, ny)[0])
+
+
 def test_step_host_rejects_bad_calls():
     with shf.Grid(32, 32, 1.0, FP64) as g:
         g.set_params(1, 1, 1, 1, 1, 1, 0.01, 0.005)
