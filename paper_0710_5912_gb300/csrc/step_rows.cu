@@ -11,9 +11,10 @@ namespace shf {
 // per row pair.  Each item stages the two real rows (a, b) in shared memory and
 // transforms a + i b (for f the staged phi rows are cubed on the fly), so every
 // output chunk of the pair is one whole 32-byte piece.
-template <class T, int LN, int P>
+template <class T, int LN, int P, int MODE>
 __global__ void __launch_bounds__(rowfwd_cta_threads(P), rowfwd_min_ctas<T>(P)) k_rowfwd(const MemberDesc* __restrict__ descs, int log2ny,
-                                                               const cplx<T>* __restrict__ tw, int mode) {
+                                                               const cplx<T>* __restrict__ tw) {
+  constexpr int mode = MODE;
   constexpr int log2nx = LN;
   using C = cplx<T>;
   constexpr int LC = Layout<T>::LC;
@@ -118,9 +119,10 @@ __device__ __forceinline__ void load16(const double2* p, double2 (&v)[1]) { v[0]
 // Nyquist coefficients / nx.
 // P = 16 (FP32): 256-thread CTAs, two per SM (128 registers), and the
 // increment bases are loaded after the transform to keep registers free.
-template <class T, int LN, int P>
+template <class T, int LN, int P, int MODE>
 __global__ void __launch_bounds__(rowfwd_cta_threads(P), P == 16 ? 2 : min_ctas<T>()) k_rowinv(
-    const MemberDesc* __restrict__ descs, int log2ny, const cplx<T>* __restrict__ tw, int mode) {
+    const MemberDesc* __restrict__ descs, int log2ny, const cplx<T>* __restrict__ tw) {
+  constexpr int mode = MODE;
   constexpr int log2nx = LN;
   using C = cplx<T>;
   constexpr int LC = Layout<T>::LC;
@@ -246,57 +248,47 @@ __global__ void __launch_bounds__(rowfwd_cta_threads(P), P == 16 ? 2 : min_ctas<
 }
 
 // ----------------------------------------------------------------- launchers
-// the forward-row kernel of variant P (points per thread); FP64 has P = 8 only
+// the row kernels by variant P (points per thread; FP64 has P = 8 only) and
+// mode (0: phi, 1: g or flow), each compiled separately
 template <class T, int LN>
-const void* rowfwd_fn(int P) {
+const void* rowfwd_fn(int P, int mode) {
   if constexpr (sizeof(T) == 4) {
-    if (P == 16) return (const void*)k_rowfwd<T, LN, 16>;
+    if (P == 16) return mode == 0 ? (const void*)k_rowfwd<T, LN, 16, 0> : (const void*)k_rowfwd<T, LN, 16, 1>;
   }
-  return (const void*)k_rowfwd<T, LN, 8>;
+  return mode == 0 ? (const void*)k_rowfwd<T, LN, 8, 0> : (const void*)k_rowfwd<T, LN, 8, 1>;
 }
-
 template <class T, int LN>
-const void* rowinv_fn(int P) {
+const void* rowinv_fn(int P, int mode) {
   if constexpr (sizeof(T) == 4) {
-    if (P == 16) return (const void*)k_rowinv<T, LN, 16>;
+    if (P == 16) return mode == 0 ? (const void*)k_rowinv<T, LN, 16, 0> : (const void*)k_rowinv<T, LN, 16, 1>;
   }
-  return (const void*)k_rowinv<T, LN, 8>;
+  return mode == 0 ? (const void*)k_rowinv<T, LN, 8, 0> : (const void*)k_rowinv<T, LN, 8, 1>;
 }
 
 template <class T>
 void launch_row_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int log2ny, const cplx<T>* tw,
                        const LaunchCfg& c, cudaStream_t st) {
   const dim3 grid(c.grid_x, nmem);
+  const bool fwd = kind == KIND_ROWFWD_PHI || kind == KIND_ROWFWD_G;
+  const int mode = (kind == KIND_ROWFWD_PHI || kind == KIND_ROWINV_PHI) ? 0 : 1;
   with_log2n(log2nx, [&](auto L) {
     constexpr int LN = decltype(L)::value;
-    const int mode = (kind == KIND_ROWFWD_PHI || kind == KIND_ROWINV_PHI) ? 0 : 1;
-    if (kind == KIND_ROWFWD_PHI || kind == KIND_ROWFWD_G) {
-      if constexpr (sizeof(T) == 4) {
-        if (c.variant == 16) {
-          k_rowfwd<T, LN, 16><<<grid, c.threads, c.smem, st>>>(d, log2ny, tw, mode);
-          return;
-        }
-      }
-      k_rowfwd<T, LN, 8><<<grid, c.threads, c.smem, st>>>(d, log2ny, tw, mode);
-    } else {
-      if constexpr (sizeof(T) == 4) {
-        if (c.variant == 16) {
-          k_rowinv<T, LN, 16><<<grid, c.threads, c.smem, st>>>(d, log2ny, tw, mode);
-          return;
-        }
-      }
-      k_rowinv<T, LN, 8><<<grid, c.threads, c.smem, st>>>(d, log2ny, tw, mode);
-    }
+    const void* f = fwd ? rowfwd_fn<T, LN>(c.variant, mode) : rowinv_fn<T, LN>(c.variant, mode);
+    const MemberDesc* dd = d;
+    const cplx<T>* tt = tw;
+    void* args[] = {(void*)&dd, (void*)&log2ny, (void*)&tt};
+    cudaLaunchKernel(f, grid, dim3(c.threads), args, c.smem, st);
   });
 }
 
 template <class T>
 int row_kernel_occupancy(int kind, int log2nx, int variant, int threads, size_t smem) {
   int nb = 0;
+  const bool fwd = kind == KIND_ROWFWD_PHI || kind == KIND_ROWFWD_G;
+  const int mode = (kind == KIND_ROWFWD_PHI || kind == KIND_ROWINV_PHI) ? 0 : 1;
   with_log2n(log2nx, [&](auto L) {
     constexpr int LN = decltype(L)::value;
-    const void* f = (kind == KIND_ROWFWD_PHI || kind == KIND_ROWFWD_G) ? rowfwd_fn<T, LN>(variant)
-                                                                        : rowinv_fn<T, LN>(variant);
+    const void* f = fwd ? rowfwd_fn<T, LN>(variant, mode) : rowinv_fn<T, LN>(variant, mode);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads, smem) != cudaSuccess) nb = 1;
   });
   return nb < 1 ? 1 : nb;
@@ -307,10 +299,11 @@ void set_row_smem_limits(int lim) {
   for (int ln = 4; ln <= LOG2_NMAX; ++ln)
     with_log2n(ln, [&](auto L) {
       constexpr int LN = decltype(L)::value;
-      cudaFuncSetAttribute(rowfwd_fn<T, LN>(8), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-      cudaFuncSetAttribute(rowfwd_fn<T, LN>(16), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-      cudaFuncSetAttribute(rowinv_fn<T, LN>(8), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-      cudaFuncSetAttribute(rowinv_fn<T, LN>(16), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      for (int P : {8, 16})
+        for (int mode : {0, 1}) {
+          cudaFuncSetAttribute(rowfwd_fn<T, LN>(P, mode), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+          cudaFuncSetAttribute(rowinv_fn<T, LN>(P, mode), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        }
     });
 }
 
