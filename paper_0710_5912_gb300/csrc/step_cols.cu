@@ -38,11 +38,11 @@ struct ColConsts {
         ny(ny_), stokes(D.stokes != 0) {}
 };
 
-// Quotients of the flow multipliers: FP32 takes the hardware reciprocal
+// Quotients of the multipliers: FP32 takes the hardware reciprocal
 // (__fdividef, within 2 ulp; the divisors here lie in [1e-12, 1e3]), FP64 the
 // IEEE quotient.
-__device__ __forceinline__ float flow_div(float a, float b) { return __fdividef(a, b); }
-__device__ __forceinline__ double flow_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float quot(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double quot(double a, double b) { return a / b; }
 
 // The multiplier at mode (m, row nn) of the column transform, in place, for a
 // compile-time pass kind (0: phi; 1: inertial flow; 2: Stokes flow):
@@ -66,14 +66,14 @@ __device__ __forceinline__ void col_multiply_k(const ColConsts<T>& K, int m, T q
       const T c4 = K.ckM * (k2 * k2);
       const T aa = K.caM * k2 - T(2) * c4;
       const T bbm = K.cbM * k2;
-      const T inv = norm / (T(1) + c4);
+      const T inv = quot(norm, T(1) + c4);
       va = C{(aa * P.x - bbm * F.x) * inv, (aa * P.y - bbm * F.y) * inv};
     }
   } else {
     const bool zero = nyq_row || (m == 0 && nn == 0);
     const C G = va;
     if (KIND == 2) {
-      const T inv = zero ? T(0) : flow_div(norm, k2 * k2);
+      const T inv = zero ? T(0) : quot(norm, k2 * k2);
       va = C{G.x * inv, G.y * inv};
     } else {
       const C Wv = vb;
@@ -82,9 +82,9 @@ __device__ __forceinline__ void col_multiply_k(const ColConsts<T>& K, int m, T q
         vb = C{-Wv.x * norm, -Wv.y * norm};             // omega^{n+1} -> 0 there
       } else {
         const T cc = K.cnu * k2;
-        const T inv = flow_div(T(1), T(1) + cc);
+        const T inv = quot(T(1), T(1) + cc);
         const C dw = C{(-T(2) * cc * Wv.x + K.dt * G.x) * inv, (-T(2) * cc * Wv.y + K.dt * G.y) * inv};
-        const T ik = flow_div(norm, k2);
+        const T ik = quot(norm, k2);
         va = C{(Wv.x + dw.x) * ik, (Wv.y + dw.y) * ik};
         vb = C{dw.x * norm, dw.y * norm};
       }
