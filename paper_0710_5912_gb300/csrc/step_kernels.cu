@@ -278,6 +278,8 @@ __device__ __forceinline__ void stencil2_body(const MemberDesc& D, const T* tp, 
   const T a = (T)D.a, b = (T)D.b, kappa = (T)D.kappa;
   const T ih2 = (T)D.inv_h2, i4h2 = (T)D.inv_4h2, inv2h = (T)D.inv_2h;
   const T cxx = T(1) + sc.s * sc.s, cxy = T(2) * sc.s;
+  // kappa and the difference scalings folded into the three Laplacian weights
+  const T kxx = kappa * cxx * ih2, kxy = kappa * cxy * i4h2, kyy = kappa * ih2;
   // mu tile row rm <-> y0 - 1 + rm <-> phi tile row rm + 1; mu quad at tile col 4 (k + 1).
   // Work unit: one quad column k over RPT consecutive mu rows, with a three-row
   // window of phi (one new phi row per mu row).
@@ -298,11 +300,11 @@ __device__ __forceinline__ void stencil2_body(const MemberDesc& D, const T* tp, 
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
         const T pc = Cn.v[p + 1];
-        const T dxx = (Cn.v[p + 2] - T(2) * pc + Cn.v[p]) * ih2;
-        const T dyy = (Un.v[p + 1] - T(2) * pc + Dn.v[p + 1]) * ih2;
-        const T dxy = (Un.v[p + 2] - Dn.v[p + 2] - Un.v[p] + Dn.v[p]) * i4h2;
-        const T lap = cxx * dxx - cxy * dxy + dyy;
-        m[p] = -a * pc + b * ((pc * pc) * pc) - kappa * lap;
+        const T sxx = Cn.v[p + 2] - T(2) * pc + Cn.v[p];          // unscaled second differences
+        const T syy = Un.v[p + 1] - T(2) * pc + Dn.v[p + 1];
+        const T sxy = Un.v[p + 2] - Dn.v[p + 2] - Un.v[p] + Dn.v[p];
+        const T klap = kxx * sxx - kxy * sxy + kyy * syy;          // kappa L_s phi
+        m[p] = pc * (b * (pc * pc) - a) - klap;
       }
       st4(tm + rm * W + c, m[0], m[1], m[2], m[3]);
       Dn = Cn;
