@@ -354,6 +354,17 @@ int ensure_pinned(shf_grid* o, size_t count) {
   return SHF_OK;
 }
 
+// Forget the captured graph (the next run of >= kGraphSteps steps captures
+// a new one): needed when the members' parameters change, because the flow
+// column pass is chosen on the host from their regimes.
+int drop_graph(shf_grid* o) {
+  if (!o->graph) return SHF_OK;
+  SHF_CUDA(o, cudaStreamSynchronize(o->stream));
+  cudaGraphExecDestroy(o->graph);
+  o->graph = nullptr;
+  return SHF_OK;
+}
+
 void free_all(shf_grid* g) {
   if (!g) return;
   cudaSetDevice(g->device);
@@ -1026,11 +1037,8 @@ int shf_set_params(shf_grid* g, double a, double b, double kappa, double M, doub
     rc = upload_desc(o, r);
     if (rc) return fail(g, rc, o->err);
   }
-  if (o->graph) {                                       // the flow pass kernel depends on the regimes
-    SHF_CUDA(g, cudaStreamSynchronize(o->stream));
-    cudaGraphExecDestroy(o->graph);
-    o->graph = nullptr;
-  }
+  rc = drop_graph(o);                                   // the flow pass kernel depends on the regimes
+  if (rc) return fail(g, rc, o->err);
   return SHF_OK;
 }
 
@@ -1443,6 +1451,7 @@ int shf_load(shf_grid* g, const char* path) {
     m.params_set = true;
   }
   int rc = upload_desc(g, 0);
+  if (!rc) rc = drop_graph(g);                           // the parameters may have changed regime
   if (rc) return rc;
   return shf_set_step(g, h.n);
 }

@@ -295,6 +295,33 @@ def test_checkpoint_resume_is_bit_identical(prec, rho, tmp_path):
         assert np.array_equal(x, y)
 
 
+def test_checkpoint_load_across_regimes_after_graph(tmp_path):
+    """Loading an inertial checkpoint into a grid that captured a Stokes graph
+    must drop that graph: the flow column pass is chosen per regime."""
+    nx, ny = 64, 32
+    pi = oracle.Params(rho=1.0, gdot=0.05, dt=0.01)
+    ps = oracle.Params(rho=0.0, gdot=0.05, dt=0.01)
+    path = tmp_path / "inertial.shf"
+    with shf.Grid(nx, ny, 1.0, FP32) as g:
+        g.set_params(pi.a, pi.b, pi.kappa, pi.M, pi.eta, pi.rho, pi.gdot, pi.dt)
+        g.set_fields(*rough_state(nx, ny, 43))
+        g.step(100)
+        g.save(path)
+    with shf.Grid(nx, ny, 1.0, FP32) as ref:
+        ref.load(path)
+        ref.step(100)
+        want = ref.get_fields()
+    with shf.Grid(nx, ny, 1.0, FP32) as g2:
+        g2.set_params(ps.a, ps.b, ps.kappa, ps.M, ps.eta, ps.rho, ps.gdot, ps.dt)
+        g2.set_fields(*rough_state(nx, ny, 44, False))
+        g2.step(100)                                    # captures a Stokes graph
+        g2.load(path)
+        g2.step(100)
+        got = g2.get_fields()
+    for x, y in zip(got, want):
+        assert np.array_equal(x, y)
+
+
 def test_checkpoint_errors(tmp_path):
     with shf.Grid(32, 32, 1.0, FP32) as g:
         g.set_params()
