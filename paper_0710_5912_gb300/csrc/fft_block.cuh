@@ -222,8 +222,9 @@ __device__ void fft_smem(C* const (&buf)[NB], int log2N, int tid, const C* __res
 // transform ends in registers with v[q] = X[t + T q].  Only the stages in
 // between exchange through shared memory.  Exchange buffers are padded by one
 // element per 16 (index i -> i + i/16), which keeps the scatter of the early
-// stages free of bank conflicts.  Eight points per thread (more threads, more
-// resident warps) measured faster on GB300 than sixteen with one stage less.
+// stages free of bank conflicts.  The column passes use eight points per
+// thread (P = 16 with one mode per instance measured no faster there); the
+// FP32 row passes use sixteen, one exchange fewer, which measured faster.
 constexpr int kP = 8;
 constexpr int kLogP = 3;
 

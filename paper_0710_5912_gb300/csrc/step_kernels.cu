@@ -32,12 +32,13 @@
 // This file holds the stencils and the launch dispatch; the transform kernels
 // are in step_rows.cu and step_cols.cu (compiled per transform length).
 //
-// Execution: the stencils run on 2D tiles, 4 x 4 outputs per thread; the
+// Execution: the FP32 stage-1 stencil (nx >= 128) streams row strips through
+// registers; the other stencils run on 2D tiles, 4 x 4 outputs per thread; the
 // transform kernels are persistent -- every instance walks its work items (row
 // pairs or column chunks) with a grid stride and, while transforming one item,
 // streams the next item's input into a shared-memory staging buffer with
 // cp.async, so the loads in flight hold shared memory rather than registers.
-// The FFT keeps 8 (or, in the FP32 forward rows, 16) points per thread in
+// The FFT keeps 8 (or, in the FP32 row passes, 16) points per thread in
 // registers (fft_block.cuh).
 //
 // Layout: real fields ny x nx row-major.  x-spectral buffers hold, for each row
