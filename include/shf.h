@@ -200,7 +200,7 @@ int shf_autotune(shf_grid* g, const char* cache_path, int* choices, int nchoices
 /* Checkpoint: a header (magic, version, sizes, precision, remap mode,
  * parameters, n, CRC-32 of the payload) and phi, psi, omega in the grid's
  * precision, so that a resumed run is bit-identical to an uninterrupted one.
- * shf_load requires a grid of the same nx, ny and precision; a missing,
+ * shf_load requires a grid of the same nx, ny, dx and precision (else SHF_EINVAL); a missing,
  * truncated or corrupt file gives SHF_EIO and leaves the grid untouched. */
 int shf_save(shf_grid* g, const char* path);
 int shf_load(shf_grid* g, const char* path);
@@ -234,18 +234,24 @@ int shf_noise_fill(double* out, int64_t count, uint64_t seed, double amp);
  *     rejected with SHF_EINVAL before any device work.
  *   cuda_stream: cudaStream_t to run on (NULL: the legacy default stream); the
  *     call synchronises it before returning.
- *   mean_phi: receives the mean (NaN on any error).
+ *   mean_phi: receives the mean; set to NaN first, so it holds NaN after any
+ *     error.
  * Same reductions as shf_mass (1024-CTA Neumaier partials folded in CTA
  * order), so for the same field both return the same bits.  Allocates
  * nothing: the partials live in a fixed 24,600-byte device array of the
- * library (one per device), found with cudaGetSymbolAddress on each call.
- * That array is shared by all calls on a device, so calls that overlap in
- * time on one device (from several host threads) race and must be serialised
- * by the caller; calls from one thread never overlap, since each returns only
- * after its stream has drained.  Returns SHF_EINVAL for NULL pointers, a bad
- * precision, sizes out of range, a misaligned or host pointer; SHF_ECUDA for
- * a CUDA failure; SHF_ENONFINITE (mean NaN) if the field holds NaN or Inf.
- * No grid is involved, so shf_last_error has no message for it. */
+ * library, which every device that loads the library holds until the process
+ * exits.  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress, with the field's device current) and keeps it; make
+ * that first call before any stream capture.  The array is shared by all
+ * calls on a device and keeps the last call's contents (the result slot is
+ * reset at the start of each call), so calls that overlap in time on one
+ * device (from several host threads) race and must be serialised by the
+ * caller; calls from one thread never overlap, since each returns only after
+ * its stream has drained.  A launch error left pending on the calling thread
+ * by earlier work is cleared on entry.  Returns SHF_EINVAL for NULL pointers,
+ * a bad precision, sizes out of range, a misaligned or host pointer;
+ * SHF_ECUDA for a CUDA failure; SHF_ENONFINITE (mean NaN) if the field holds
+ * NaN or Inf.  No grid is involved, so shf_last_error has no message for it. */
 int shf_mass_static(const void* d_field, int precision, int nx, int ny, void* cuda_stream, double* mean_phi);
 
 #ifdef __cplusplus

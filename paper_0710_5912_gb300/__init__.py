@@ -86,8 +86,16 @@ def shf_noise_fill(count, seed, amp):
 
 
 def shf_mass_static(d_field, precision, nx, ny, stream=None):
-    """Mean of a device field (pointer or tensor) without device allocation."""
+    """Mean of a device field (pointer or tensor) without device allocation.
+
+    With a torch tensor and no stream, the call runs on torch's current stream
+    of the tensor's device, so it is ordered after the work that wrote the
+    tensor there; with a raw pointer and no stream it runs on the legacy
+    default stream."""
     ptr = int(d_field.data_ptr()) if hasattr(d_field, "data_ptr") else d_field
+    if stream is None and hasattr(d_field, "device") and getattr(d_field.device, "type", "") == "cuda":
+        import torch
+        stream = torch.cuda.current_stream(d_field.device)
     m = ctypes.c_double()
     _check(lib().shf_mass_static(ptr, int(precision), int(nx), int(ny), _stream_handle(stream),
                                  ctypes.byref(m)), what="shf_mass_static")
@@ -131,12 +139,13 @@ def shf_step(h, nsteps=1):
     _check(lib().shf_step(h, int(nsteps)), h, "shf_step")
 
 
-KERNEL_KINDS = ("stencil1", "rowfwd_phi", "colpass_phi", "rowinv_phi", "stencil2", "rowfwd_g",
+KERNEL_KINDS = ("stencil1", "rowfwd_phi", "colpass_phi", "rowinv_phi", "stencil2", "rowfwd_g", "lowmode",
                 "colpass_flow", "rowinv_flow")
 
 
 def shf_profile_step(h, nsteps):
-    """Mean device ms per step of each of the six launches of a step."""
+    """Mean device ms per step of each launch kind of a step ("lowmode" runs for
+    FP32 grids only; 0 for FP64)."""
     out = np.zeros(len(KERNEL_KINDS))
     _check(lib().shf_profile_step(h, int(nsteps), _dptr(out), len(KERNEL_KINDS)), h, "shf_profile_step")
     return dict(zip(KERNEL_KINDS, out.tolist()))

@@ -67,8 +67,79 @@ __global__ void k_convert_out(const T* __restrict__ src, double* __restrict__ ds
     dst[e] = (double)src[e];
 }
 
-// out[3*cta + 0..2] = (sum, compensation, non-finite count) over this CTA's
-// grid-stride share of f.
+// Knuth's TwoSum: s + e equals a + b exactly (round to nearest, no overflow),
+// with s = fl(a + b); explicit round-to-nearest additions keep the compiler
+// from reordering it.
+__device__ __forceinline__ float two_sum(float a, float b, float& e) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return s;
+}
+// 1 if x is NaN or +-Inf (all exponent bits set), from the bits alone
+__device__ __forceinline__ unsigned nonfinite_bit(float x) {
+  return (__float_as_uint(x) & 0x7f800000u) == 0x7f800000u;
+}
+
+// FP32 fields: out[3*cta + 0..2] = (sum, compensation, non-finite count) over
+// this CTA's grid-stride share of f.  A thread reads 16-byte vectors, two per
+// group of eight values (one from each of two consecutive grid strides, so
+// every load is coalesced), and sums a group exactly as a float pair by a tree
+// of TwoSums: the head goes into a double accumulator by one plain addition
+// (the only double-precision operation per eight values), the tails into a
+// float one.  Each double addition rounds at most half an ulp of the thread's
+// running sum, so the thread total is within a few 1e-16 of its exact sum
+// relative to its magnitude; threads and CTAs are then combined with
+// Neumaier's compensated sum.  Fixed order throughout: for one field and
+// launch shape the result is always the same bits.
+__global__ void __launch_bounds__(256) k_mass_partials_f32(const float* __restrict__ f, long long count,
+                                                           double* __restrict__ out) {
+  __shared__ double sh[2 * 2 * 32];
+  double acc = 0.0;
+  float tail = 0.f;
+  unsigned bad = 0;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long n4 = (reinterpret_cast<uintptr_t>(f) & 15) == 0 ? count / 4 : 0;
+  const float4* f4 = reinterpret_cast<const float4*>(f);
+  long long e = tid;
+  for (; e + stride < n4; e += 2 * stride) {
+    const float4 a = __ldcs(f4 + e), b = __ldcs(f4 + e + stride);
+    bad |= nonfinite_bit(a.x) | nonfinite_bit(a.y) | nonfinite_bit(a.z) | nonfinite_bit(a.w) |
+           nonfinite_bit(b.x) | nonfinite_bit(b.y) | nonfinite_bit(b.z) | nonfinite_bit(b.w);
+    float e0, e1, e2, e3, e4, e5, e6;
+    const float s01 = two_sum(a.x, a.y, e0), s23 = two_sum(a.z, a.w, e1);
+    const float s45 = two_sum(b.x, b.y, e2), s67 = two_sum(b.z, b.w, e3);
+    const float s03 = two_sum(s01, s23, e4), s47 = two_sum(s45, s67, e5);
+    const float h = two_sum(s03, s47, e6);
+    acc += (double)h;
+    tail += (((e0 + e1) + (e2 + e3)) + (e4 + e5)) + e6;
+  }
+  if (e < n4) {
+    const float4 a = __ldcs(f4 + e);
+    bad |= nonfinite_bit(a.x) | nonfinite_bit(a.y) | nonfinite_bit(a.z) | nonfinite_bit(a.w);
+    float e0, e1, e2;
+    const float s01 = two_sum(a.x, a.y, e0), s23 = two_sum(a.z, a.w, e1);
+    const float h = two_sum(s01, s23, e2);
+    acc += (double)h;
+    tail += (e0 + e1) + e2;
+  }
+  for (long long k = 4 * n4 + tid; k < count; k += stride) {   // the rest (or an unaligned field)
+    const float v = f[k];
+    bad |= nonfinite_bit(v);
+    acc += (double)v;
+  }
+  double s[2] = {acc, bad ? 1.0 : 0.0}, c[2] = {(double)tail, 0.0};
+  block_reduce_pairs<2>(s, c, sh);
+  if (threadIdx.x == 0) {
+    out[3 * blockIdx.x + 0] = s[0];
+    out[3 * blockIdx.x + 1] = c[0];
+    out[3 * blockIdx.x + 2] = s[1] + c[1];
+  }
+}
+
+// FP64 fields: out[3*cta + 0..2] = (sum, compensation, non-finite count) over
+// this CTA's grid-stride share of f, one Neumaier addition per value.
 template <class T>
 __global__ void __launch_bounds__(256) k_mass_partials(const T* __restrict__ f, long long count,
                                                        double* __restrict__ out) {
@@ -85,6 +156,39 @@ __global__ void __launch_bounds__(256) k_mass_partials(const T* __restrict__ f, 
     out[3 * blockIdx.x + 0] = s[0];
     out[3 * blockIdx.x + 1] = c[0];
     out[3 * blockIdx.x + 2] = s[1] + c[1];
+  }
+}
+
+// Fold of the per-CTA mass partials into out[0..2] = (sum, compensation,
+// non-finite count), in a fixed two-level order: lane l of one warp folds
+// partials [l G, (l + 1) G) in order (G = ceil(ctas / 32)) with Neumaier's
+// steps, then lane 0 folds the 32 lane results in lane order.  Every caller
+// (shf_mass, shf_sync, shf_mass_static) uses this one fold, so they agree
+// bit for bit on the same field.
+__global__ void k_mass_fold(const double* __restrict__ part, int ctas, double* __restrict__ out) {
+  __shared__ double sh[3 * 32];
+  const int lane = threadIdx.x;
+  const int G = (ctas + 31) / 32;
+  double s = 0.0, c = 0.0, nf = 0.0;
+  for (int b = lane * G; b < (lane + 1) * G && b < ctas; ++b) {
+    neumaier_add(s, c, part[3 * b]);
+    c += part[3 * b + 1];
+    nf += part[3 * b + 2];
+  }
+  sh[lane] = s;
+  sh[32 + lane] = c;
+  sh[64 + lane] = nf;
+  __syncwarp();
+  if (lane == 0) {
+    double S = 0.0, C = 0.0, NF = 0.0;
+    for (int l = 0; l < 32; ++l) {
+      neumaier_add(S, C, sh[l]);
+      C += sh[32 + l];
+      NF += sh[64 + l];
+    }
+    out[0] = S;
+    out[1] = C;
+    out[2] = NF;
   }
 }
 
@@ -227,8 +331,12 @@ int launch_mass_partials(const T* f, long long count, double* out, int max_ctas,
   long long ctas = (count + thr - 1) / thr;
   if (ctas > max_ctas) ctas = max_ctas;
   if (ctas < 1) ctas = 1;
-  k_mass_partials<T><<<(int)ctas, thr, 0, st>>>(f, count, out);
+  if constexpr (sizeof(T) == 4) k_mass_partials_f32<<<(int)ctas, thr, 0, st>>>(f, count, out);
+  else k_mass_partials<T><<<(int)ctas, thr, 0, st>>>(f, count, out);
   return (int)ctas;
+}
+void launch_mass_fold(const double* partials, int ctas, double* out, cudaStream_t st) {
+  k_mass_fold<<<1, 32, 0, st>>>(partials, ctas, out);
 }
 template <class T>
 void launch_sf_rows(const T* phi, cplx<T>* xs, int log2nx, int log2ny, const cplx<T>* tw, const RowCfg& c,

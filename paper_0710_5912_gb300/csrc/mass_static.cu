@@ -1,11 +1,12 @@
 // shf_mass_static: the mean of a caller-owned device field without any device
-// allocation.  It runs the same two reductions as shf_mass (per-CTA Neumaier
-// partials over the same number of CTAs, then a fold of the partials in CTA
-// order), so both return the same bits for the same field; the partials live
-// in a fixed file-scope device array instead of a lazily allocated buffer, and
-// the fold runs on the device so that only three doubles come back.
+// allocation.  It runs the same two reductions as shf_mass (per-CTA partials
+// over the same number of CTAs, then the same fixed-order fold of the
+// partials on the device), so both return the same bits for the same field;
+// the partials live in a fixed file-scope device array instead of the grid's
+// lazily allocated scratch, and only three doubles come back.
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 
 #include "../../include/shf.h"
 #include "shf_internal.cuh"
@@ -23,37 +24,35 @@ constexpr int kStaticSlots = kResultSlot + 3;   // 24,600 bytes per device
 
 static __device__ __align__(256) double g_mass_scratch[kStaticSlots];
 
-// Fold the partials in CTA order with the same Neumaier steps, in the same
-// order, as shf_mass's host-side fold: one thread, so the result is fixed.
-__global__ void k_fold_mass_partials(const double* __restrict__ part, int ctas, double* __restrict__ out) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  double s = 0.0, c = 0.0, nf = 0.0;
-  for (int b = 0; b < ctas; ++b) {
-    const double v = part[3 * b];
-    const double t = s + v;
-    if (fabs(s) >= fabs(v)) c += (s - t) + v;
-    else c += (v - t) + s;
-    s = t;
-    c += part[3 * b + 1];
-    nf += part[3 * b + 2];
+// Device address of g_mass_scratch on each device, looked up once per device
+// (with that device current) by the first call that runs there.  In host code
+// the name g_mass_scratch is only a host-side stand-in, so kernels get this
+// address, never the name.
+constexpr int kMaxDevices = 64;
+std::mutex g_addr_mutex;
+double* g_addr[kMaxDevices] = {};
+
+// the scratch address on the current device `dev`; nullptr if the lookup fails
+double* scratch_on(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lock(g_addr_mutex);
+  if (!g_addr[dev]) {
+    void* sym = nullptr;
+    if (cudaGetSymbolAddress(&sym, g_mass_scratch) != cudaSuccess || !sym) return nullptr;
+    g_addr[dev] = static_cast<double*>(sym);
   }
-  out[0] = s;
-  out[1] = c;
-  out[2] = nf;
+  return g_addr[dev];
 }
 
 template <class T>
-int mass_static_t(const void* d_field, long long count, cudaStream_t st, double* res) {
-  void* sym = nullptr;
-  if (cudaGetSymbolAddress(&sym, g_mass_scratch) != cudaSuccess || !sym) return SHF_ECUDA;
-  double* scratch = static_cast<double*>(sym);
+int mass_static_t(double* scratch, const void* d_field, long long count, cudaStream_t st, double* res) {
   // The partial slots are all written by the partial pass before the fold
   // reads them; only the result slot is reset (to NaN bytes) so that a failed
   // pass can never hand back a previous call's result.
   if (cudaMemsetAsync(scratch + kResultSlot, 0xFF, 3 * sizeof(double), st) != cudaSuccess) return SHF_ECUDA;
   const int ctas = launch_mass_partials<T>(static_cast<const T*>(d_field), count, scratch, kStaticMassCtas, st);
   if (cudaGetLastError() != cudaSuccess) return SHF_ECUDA;
-  k_fold_mass_partials<<<1, 32, 0, st>>>(scratch, ctas, scratch + kResultSlot);
+  launch_mass_fold(scratch, ctas, scratch + kResultSlot, st);
   if (cudaGetLastError() != cudaSuccess) return SHF_ECUDA;
   if (cudaMemcpyAsync(res, scratch + kResultSlot, 3 * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
     return SHF_ECUDA;
@@ -65,12 +64,16 @@ int mass_static_t(const void* d_field, long long count, cudaStream_t st, double*
 
 extern "C" int shf_mass_static(const void* d_field, int precision, int nx, int ny, void* cuda_stream,
                                double* mean_phi) {
-  if (!mean_phi || !d_field) return SHF_EINVAL;
+  if (!mean_phi) return SHF_EINVAL;
+  *mean_phi = NAN;
+  if (!d_field) return SHF_EINVAL;
   if (precision != SHF_FP32 && precision != SHF_FP64) return SHF_EINVAL;
   if (nx < 1 || ny < 1 || nx > kStaticMaxSide || ny > kStaticMaxSide) return SHF_EINVAL;
   const size_t esize = precision == SHF_FP64 ? sizeof(double) : sizeof(float);
   if (reinterpret_cast<uintptr_t>(d_field) % esize != 0) return SHF_EINVAL;
-  *mean_phi = NAN;
+  // a launch error left pending by earlier work on this thread is cleared
+  // here, so that the check after this call's launches reports only its own
+  cudaGetLastError();
 
   cudaPointerAttributes attr;
   if (cudaPointerGetAttributes(&attr, d_field) != cudaSuccess) {
@@ -85,8 +88,11 @@ extern "C" int shf_mass_static(const void* d_field, int precision, int nx, int n
   double res[3] = {NAN, NAN, NAN};
   const long long count = (long long)nx * ny;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  const int rc = precision == SHF_FP64 ? mass_static_t<double>(d_field, count, st, res)
-                                       : mass_static_t<float>(d_field, count, st, res);
+  double* scratch = scratch_on(attr.device);
+  int rc = SHF_ECUDA;
+  if (scratch)
+    rc = precision == SHF_FP64 ? mass_static_t<double>(scratch, d_field, count, st, res)
+                               : mass_static_t<float>(scratch, d_field, count, st, res);
   if (attr.device != prev) cudaSetDevice(prev);
   if (rc != SHF_OK) return rc;
   if (res[2] > 0.0 || !(res[2] == res[2])) return SHF_ENONFINITE;

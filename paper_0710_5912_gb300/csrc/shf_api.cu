@@ -35,6 +35,9 @@ struct Member {
   void* phi_star = nullptr;
   void* omega_star = nullptr;
   void* nyq = nullptr;        // 2 ny reals: nyq_phi then nyq_omega
+  void* w_hat = nullptr;      // FP32: omega's 2D transform (inertial), see MemberDesc
+  void* low_rows = nullptr;   // FP32: low row modes of g
+  void* low_hat = nullptr;    // FP32: low 2D modes of g
   StepState* d_st = nullptr;  // into the owner's step-state array
   int cls = -1, slot = -1;
 };
@@ -72,6 +75,7 @@ struct shf_grid {
   StepState* d_state = nullptr;   // per member: counter and strain of the current step
   long long n = 0;
   void* d_tw = nullptr;     // W[k] = exp(2 pi i k / NMAX) (shared-memory FFTs of the diagnostics)
+  void* d_twff = nullptr;   // FP32 grids: W[k] as float pairs (hi, lo) per component, float4 per k
   void* d_twr = nullptr;    // per-stage tables of the register FFT (step kernels)
   double* d_stage = nullptr;
   size_t stage_count = 0;
@@ -82,6 +86,7 @@ struct shf_grid {
   cudaGraphExec_t graph = nullptr;
   cudaStream_t io_stream = nullptr;   // shf_step_host_f32: the early phi download
   cudaEvent_t phi_done = nullptr;     // recorded after the last step's phi row inverse
+  bool what_valid = false;            // FP32: w_hat holds the 2D transform of the current omega
   std::vector<shf_grid*> views;
   std::string err;
 };
@@ -209,7 +214,8 @@ struct Tune {
 template <class T>
 Tune resolved(const SizeClass& cl, Tune t) {
   if (t.rowfwd_phi_points == 0 || sizeof(T) == 8) t.rowfwd_phi_points = rowfwd_default_points<T>();
-  if (t.rowfwd_g_points == 0 || sizeof(T) == 8) t.rowfwd_g_points = rowfwd_default_points<T>();
+  // FP32: the g row pass takes the force's low modes from its radix-16 first stage
+  if (t.rowfwd_g_points == 0 || sizeof(T) == 8 || sizeof(T) == 4) t.rowfwd_g_points = rowfwd_default_points<T>();
   const int maxrows = cl.ny < 32 ? cl.ny : 32;
   if (t.stencil_rows == 0 || t.stencil_rows > maxrows) t.stencil_rows = maxrows;
   return t;
@@ -307,6 +313,14 @@ MemberDesc make_desc(const shf_grid* o, const Member& m) {
   d.qy_unit = two_pi / (m.ny * m.dx);
   d.remap = o->remap_mode == SHF_REMAP_SHIFT ? 1 : 0;
   d.ratio = m.nx / m.ny;
+  const bool fp32 = o->precision == SHF_FP32;
+  d.w_hat = m.w_hat;
+  d.low_rows = m.low_rows;
+  d.low_hat = m.low_hat;
+  d.wspec = fp32 && !d.stokes ? 1 : 0;
+  d.low = fp32 ? 1 : 0;
+  d.lowm = m.nx / 2 - 1 < kLowM ? m.nx / 2 - 1 : kLowM;
+  d.lown = m.ny / 2 - 1 < kLowN ? m.ny / 2 - 1 : kLowN;
   return d;
 }
 
@@ -380,10 +394,14 @@ void free_all(shf_grid* g) {
     cudaFree(m.phi_star);
     cudaFree(m.omega_star);
     cudaFree(m.nyq);
+    cudaFree(m.w_hat);
+    cudaFree(m.low_rows);
+    cudaFree(m.low_hat);
   }
   for (auto& cl : g->classes) cudaFree(cl.d_desc);
   cudaFree(g->d_state);
   cudaFree(g->d_tw);
+  cudaFree(g->d_twff);
   cudaFree(g->d_twr);
   cudaFree(g->d_stage);
   cudaFree(g->d_scratch);
@@ -453,6 +471,17 @@ int build(shf_grid* g, const std::vector<int>& nx, const std::vector<int>& ny, c
     if (cudaMalloc(&m.nyq, 2 * (size_t)m.ny * R) != cudaSuccess)
       return fail(g, SHF_ENOMEM, "field allocation failed");
     SHF_CUDA(g, cudaMemsetAsync(m.nyq, 0, 2 * (size_t)m.ny * R, g->stream));
+    if (g->precision == SHF_FP32) {
+      // w_hat: nx/2 x ny complex floats (the bytes of one real field); low modes of g
+      const size_t lr = (size_t)m.ny * (kLowM + 1) * sizeof(float2);
+      const size_t lh = (size_t)(kLowM + 1) * (2 * kLowN + 1) * sizeof(float2);
+      if (cudaMalloc(&m.w_hat, bytes) != cudaSuccess || cudaMalloc(&m.low_rows, lr) != cudaSuccess ||
+          cudaMalloc(&m.low_hat, lh) != cudaSuccess)
+        return fail(g, SHF_ENOMEM, "field allocation failed");
+      SHF_CUDA(g, cudaMemsetAsync(m.w_hat, 0, bytes, g->stream));
+      SHF_CUDA(g, cudaMemsetAsync(m.low_rows, 0, lr, g->stream));
+      SHF_CUDA(g, cudaMemsetAsync(m.low_hat, 0, lh, g->stream));
+    }
     int found = -1;
     for (size_t c = 0; c < g->classes.size(); ++c)
       if (g->classes[c].nx == m.nx && g->classes[c].ny == m.ny) found = (int)c;
@@ -512,6 +541,19 @@ int build(shf_grid* g, const std::vector<int>& nx, const std::vector<int>& ny, c
   if (rc2) return rc2;
   rc2 = upload(&g->d_twr, twr);
   if (rc2) return rc2;
+  if (g->precision == SHF_FP32) {
+    // the low-mode column DFT's twiddles to about 2^-48: (cos hi, cos lo, sin hi, sin lo)
+    std::vector<float> ff(4 * (size_t)NMAX);
+    for (int k = 0; k < NMAX; ++k)
+      for (int c = 0; c < 2; ++c) {
+        const double v = tw[2 * k + c];
+        const float hi = (float)v;
+        ff[4 * k + 2 * c] = hi;
+        ff[4 * k + 2 * c + 1] = (float)(v - (double)hi);
+      }
+    if (cudaMalloc(&g->d_twff, ff.size() * sizeof(float)) != cudaSuccess) return fail(g, SHF_ENOMEM, "twiddles");
+    SHF_CUDA(g, cudaMemcpy(g->d_twff, ff.data(), ff.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
   SHF_CUDA(g, cudaStreamSynchronize(g->stream));
   return SHF_OK;
 }
@@ -520,6 +562,12 @@ int build(shf_grid* g, const std::vector<int>& nx, const std::vector<int>& ny, c
 template <class T>
 void launch_kind(shf_grid* o, SizeClass& cl, int kind) {
   const cplx<T>* tw = static_cast<const cplx<T>*>(o->d_twr);
+  if (kind == KIND_LOWMODE) {                           // FP32 only: the force's low 2D modes
+    if (sizeof(T) == 4)
+      launch_lowmode_cols(cl.d_desc, (int)cl.members.size(), cl.log2ny, static_cast<const float4*>(o->d_twff),
+                          o->stream);
+    return;
+  }
   LaunchCfg c = cl.cfg[kind];
   if (kind == KIND_COLPASS_FLOW) {                      // the flow pass specialised on the members' regime
     bool inertial = false, stokes = false;
@@ -538,9 +586,22 @@ void enqueue_step(shf_grid* o) {
 }
 
 // every member's StepState from its counter; needed once before a run of
-// steps (each step's last kernel then prepares the next step's state)
+// steps (each step's last kernel then prepares the next step's state).  FP32
+// grids whose fields were set from outside since their last step also get
+// w_hat, omega's 2D transform, recomputed from omega (a row pass and a column
+// pass; members without w_hat skip them).
 void enqueue_state_init(shf_grid* o) {
   for (auto& cl : o->classes) launch_step_state_init(cl.d_desc, (int)cl.members.size(), o->stream);
+  if (o->precision == SHF_FP32 && !o->what_valid) {
+    for (auto& cl : o->classes) {
+      const int nm = (int)cl.members.size();
+      launch_row_kernel<float>(KIND_ROWFWD_OMEGA, cl.d_desc, nm, cl.log2nx, cl.log2ny,
+                               static_cast<const float2*>(o->d_twr), cl.cfg[KIND_ROWFWD_G], o->stream);
+      launch_col_kernel<float>(KIND_COLPASS_WINIT, cl.d_desc, nm, cl.log2nx, cl.log2ny,
+                               static_cast<const float2*>(o->d_twr), cl.cfg[KIND_COLPASS_FLOW], o->stream);
+    }
+    o->what_valid = true;
+  }
 }
 
 void enqueue_steps(shf_grid* o, long long k) {
@@ -561,28 +622,19 @@ int member_index(shf_grid* g) { return g->kind == 2 ? g->member : 0; }
 // sum of mass partials in fixed order; returns (sum, nonfinite count)
 template <class T>
 int field_sum(shf_grid* o, const Member& m, const void* field, double* total, double* nonfinite) {
-  int rc = ensure_scratch(o, 3 * kMassCtas);
+  int rc = ensure_scratch(o, 3 * kMassCtas + 3);
   if (rc) return rc;
-  rc = ensure_pinned(o, 3 * kMassCtas);
+  rc = ensure_pinned(o, 3);
   if (rc) return rc;
   const long long count = (long long)m.nx * m.ny;
   const int ctas = launch_mass_partials<T>(static_cast<const T*>(field), count, o->d_scratch, kMassCtas, o->stream);
+  launch_mass_fold(o->d_scratch, ctas, o->d_scratch + 3 * kMassCtas, o->stream);
   SHF_CUDA(o, cudaGetLastError());
-  SHF_CUDA(o, cudaMemcpyAsync(o->h_pinned, o->d_scratch, 3 * ctas * sizeof(double), cudaMemcpyDeviceToHost,
-                              o->stream));
+  SHF_CUDA(o, cudaMemcpyAsync(o->h_pinned, o->d_scratch + 3 * kMassCtas, 3 * sizeof(double),
+                              cudaMemcpyDeviceToHost, o->stream));
   SHF_CUDA(o, cudaStreamSynchronize(o->stream));
-  double s = 0.0, c = 0.0, nf = 0.0;
-  for (int b = 0; b < ctas; ++b) {
-    const double v = o->h_pinned[3 * b];
-    const double t = s + v;
-    if (std::fabs(s) >= std::fabs(v)) c += (s - t) + v;
-    else c += (v - t) + s;
-    s = t;
-    c += o->h_pinned[3 * b + 1];
-    nf += o->h_pinned[3 * b + 2];
-  }
-  *total = s + c;
-  *nonfinite = nf;
+  *total = o->h_pinned[0] + o->h_pinned[1];
+  *nonfinite = o->h_pinned[2];
   return SHF_OK;
 }
 
@@ -613,6 +665,7 @@ namespace {
 template <class T>
 int set_fields_t(shf_grid* g, const double* phi, const double* psi, const double* omega) {
   shf_grid* o = owner(g);
+  o->what_valid = false;
   Member& m = *member_of(g);
   const size_t count = (size_t)m.nx * m.ny;
   const double* src[3] = {phi, psi, m.rho > 0 ? omega : nullptr};
@@ -1039,6 +1092,7 @@ int shf_set_params(shf_grid* g, double a, double b, double kappa, double M, doub
   }
   rc = drop_graph(o);                                   // the flow pass kernel depends on the regimes
   if (rc) return fail(g, rc, o->err);
+  o->what_valid = false;                                // a regime change makes w_hat stale
   return SHF_OK;
 }
 
@@ -1057,6 +1111,7 @@ int shf_set_fields_f32(shf_grid* g, const float* phi, const float* psi, const fl
   if (g->precision != SHF_FP32) return fail(g, SHF_EINVAL, "float fields need an FP32 grid");
   shf_grid* o = owner(g);
   SHF_CUDA(g, cudaSetDevice(o->device));
+  o->what_valid = false;
   Member& m = *member_of(g);
   const size_t bytes = (size_t)m.nx * m.ny * sizeof(float);
   const float* src[3] = {phi, psi, m.rho > 0 ? omega : nullptr};
@@ -1122,6 +1177,7 @@ int shf_bind_device_fields(shf_grid* g, void* d_phi, void* d_psi, void* d_omega)
   m.psi = d_psi;
   if (d_omega) m.omega = d_omega;
   m.bound = true;
+  g->what_valid = false;
   return upload_desc(g, 0);
 }
 
@@ -1135,6 +1191,7 @@ int shf_set_step(shf_grid* g, int64_t n) {
                               g->stream));
   SHF_CUDA(g, cudaStreamSynchronize(g->stream));
   g->n = n;
+  g->what_valid = false;                                // the next step re-reads omega
   return SHF_OK;
 }
 
@@ -1160,6 +1217,7 @@ int shf_step_host_f32(shf_grid* g, int64_t nsteps, const float* phi_in, const fl
   if (!g->phi_done) SHF_CUDA(g, cudaEventCreateWithFlags(&g->phi_done, cudaEventDisableTiming));
   const size_t bytes = (size_t)m.nx * m.ny * sizeof(float);
   if (phi_in) {
+    g->what_valid = false;
     const float* src[3] = {phi_in, psi_in, m.rho > 0 ? omega_in : nullptr};
     void* dst[3] = {m.phi, m.psi, m.omega};
     for (int f = 0; f < 3; ++f) {
@@ -1391,20 +1449,24 @@ int shf_save(shf_grid* g, const char* path) {
   SHF_CUDA(g, cudaSetDevice(g->device));
   const Member& m = g->members[0];
   const size_t bytes = (size_t)m.nx * m.ny * real_size(g);
-  std::vector<unsigned char> payload(3 * bytes);
-  const void* src[3] = {m.phi, m.psi, m.omega};
-  for (int f = 0; f < 3; ++f)
+  // FP32 inertial grids carry omega's 2D transform from step to step; it is
+  // saved too (when current), so that a resumed run continues bit for bit
+  const bool with_what = g->precision == SHF_FP32 && m.rho > 0 && g->what_valid && m.w_hat;
+  const int nblocks = with_what ? 4 : 3;
+  std::vector<unsigned char> payload(nblocks * bytes);
+  const void* src[4] = {m.phi, m.psi, m.omega, m.w_hat};
+  for (int f = 0; f < nblocks; ++f)
     SHF_CUDA(g, cudaMemcpyAsync(payload.data() + f * bytes, src[f], bytes, cudaMemcpyDeviceToHost, g->stream));
   SHF_CUDA(g, cudaStreamSynchronize(g->stream));
   CkptHeader h;
   std::memset(&h, 0, sizeof(h));
   std::memcpy(h.magic, "SHFCKPT1", 8);
-  h.version = 1;
+  h.version = 2;
   h.nx = m.nx;
   h.ny = m.ny;
   h.precision = g->precision;
   h.remap_mode = g->remap_mode;
-  h.has_params = m.params_set ? 1 : 0;
+  h.has_params = (m.params_set ? 1 : 0) | (with_what ? 2 : 0);
   const double pv[9] = {m.a, m.b, m.kappa, m.M, m.eta, m.rho, m.gdot, m.dt, m.dx};
   std::memcpy(h.params, pv, sizeof(pv));
   h.n = g->n;
@@ -1426,12 +1488,17 @@ int shf_load(shf_grid* g, const char* path) {
   const bool got = std::fread(&h, sizeof(h), 1, fp) == 1;
   Member& m = g->members[0];
   const size_t bytes = (size_t)m.nx * m.ny * real_size(g);
-  std::vector<unsigned char> payload(3 * bytes);
-  bool ok = got && std::memcmp(h.magic, "SHFCKPT1", 8) == 0 && h.version == 1 &&
+  bool ok = got && std::memcmp(h.magic, "SHFCKPT1", 8) == 0 && (h.version == 1 || h.version == 2) &&
             h.header_crc == crc32_update(0, reinterpret_cast<const unsigned char*>(&h), offsetof(CkptHeader, header_crc));
+  const bool with_what = ok && h.version == 2 && (h.has_params & 2) && g->precision == SHF_FP32 && m.w_hat;
+  std::vector<unsigned char> payload((with_what ? 4 : 3) * bytes);
   if (ok && (h.nx != m.nx || h.ny != m.ny || h.precision != g->precision)) {
     std::fclose(fp);
     return fail(g, SHF_EINVAL, "checkpoint was written for another grid size or precision");
+  }
+  if (ok && h.params[8] != m.dx) {                     // the mesh spacing is fixed at creation
+    std::fclose(fp);
+    return fail(g, SHF_EINVAL, "checkpoint was written for another mesh spacing dx");
   }
   ok = ok && std::fread(payload.data(), 1, payload.size(), fp) == payload.size();
   unsigned char extra;
@@ -1440,12 +1507,12 @@ int shf_load(shf_grid* g, const char* path) {
   if (!ok || h.payload_crc != crc32_update(0, payload.data(), payload.size()))
     return fail(g, SHF_EIO, "checkpoint truncated or corrupt");
   SHF_CUDA(g, cudaSetDevice(g->device));
-  void* dst[3] = {m.phi, m.psi, m.omega};
-  for (int f = 0; f < 3; ++f)
+  void* dst[4] = {m.phi, m.psi, m.omega, m.w_hat};
+  for (int f = 0; f < (with_what ? 4 : 3); ++f)
     SHF_CUDA(g, cudaMemcpyAsync(dst[f], payload.data() + f * bytes, bytes, cudaMemcpyHostToDevice, g->stream));
   SHF_CUDA(g, cudaStreamSynchronize(g->stream));
   g->remap_mode = h.remap_mode;
-  if (h.has_params) {
+  if (h.has_params & 1) {
     const double* p = h.params;
     m.a = p[0]; m.b = p[1]; m.kappa = p[2]; m.M = p[3]; m.eta = p[4]; m.rho = p[5]; m.gdot = p[6]; m.dt = p[7];
     m.params_set = true;
@@ -1453,7 +1520,10 @@ int shf_load(shf_grid* g, const char* path) {
   int rc = upload_desc(g, 0);
   if (!rc) rc = drop_graph(g);                           // the parameters may have changed regime
   if (rc) return rc;
-  return shf_set_step(g, h.n);
+  rc = shf_set_step(g, h.n);
+  // omega's 2D transform: restored from the file, or recomputed from omega at the next step
+  g->what_valid = with_what && m.rho > 0;
+  return rc;
 }
 
 }  // extern "C"

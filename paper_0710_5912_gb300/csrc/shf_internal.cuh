@@ -36,6 +36,15 @@ struct MemberDesc {
   void* nyq_phi;     // per row: the real Nyquist coefficient of phi*'s row DFT
   void* nyq_omega;   // per row: the same for omega*
   void* gbuf;        // g = -F/rho (or -F/eta), real; shares phi*'s storage (phi* is dead by then)
+  // FP32 members: vorticity carried in 2D spectral form and low modes of the
+  // force computed apart (see step_cols.cu).  w_hat: the 2D DFT of omega
+  // (unnormalised), nx/2 x ny complex in the column-chunk layout of the
+  // column passes; low_rows: the row DFT coefficients m = 0..lowm of g's rows,
+  // ny complex per m (element m ny + j); low_hat: the 2D DFT of g at
+  // m = 0..lowm, n = -lown..lown, (2 lown + 1) complex per m.
+  void* w_hat;
+  void* low_rows;
+  void* low_hat;
   StepState* st;  // device step counter and strain of the current step
   // parameters and derived constants (double; cast to the working precision)
   double a, b, kappa, M, eta, rho, gdot, dt, dx;
@@ -50,8 +59,20 @@ struct MemberDesc {
   int stokes;            // rho == 0
   int remap;             // 1 when the SHIFT remap is active
   int ratio;             // nx / ny
+  int wspec;             // 1: omega carried as w_hat (FP32 inertial); 0: increment form on omega*
+  int low;               // 1: the low modes of g_hat come from low_hat (FP32)
+  int lowm, lown;        // the low-mode window of this size: m <= lowm, |n| <= lown
   int pad_;
 };
+
+// Low-mode window of the force (FP32): the row transform of g takes its
+// coefficients m <= kLowM from the first radix-16 stage with compensated
+// sums, a small column DFT takes n in [-kLowN, kLowN] from them, and the flow
+// column pass uses these in place of its own transform there.  kLowM = 8 is
+// the most the row pass's exchange buffer can hold (2 (2 kLowM + 1) floats
+// per thread).
+constexpr int kLowM = 8;
+constexpr int kLowN = 16;
 
 // Strain sawtooth of Section V from the integer step n (same operation order
 // as the host and the oracle; explicit rounding intrinsics keep the compiler
@@ -110,7 +131,7 @@ template <class T> constexpr int rowfwd_min_ctas(int P) { return P == 16 ? 3 : (
 template <class T> constexpr int rowfwd_default_points() { return sizeof(T) == 4 ? 16 : 8; }
 template <class T> constexpr int rowinv_default_points() { return sizeof(T) == 4 ? 16 : 8; }
 
-// The eight launches of a step, in order.
+// The launches of a step, in order (KIND_LOWMODE runs for FP32 classes only).
 enum StepKind {
   KIND_STENCIL1 = 0,
   KIND_ROWFWD_PHI = 1,
@@ -118,10 +139,14 @@ enum StepKind {
   KIND_ROWINV_PHI = 3,
   KIND_STENCIL2 = 4,
   KIND_ROWFWD_G = 5,
-  KIND_COLPASS_FLOW = 6,
-  KIND_ROWINV_FLOW = 7,
-  KIND_COUNT = 8
+  KIND_LOWMODE = 6,
+  KIND_COLPASS_FLOW = 7,
+  KIND_ROWINV_FLOW = 8,
+  KIND_COUNT = 9
 };
+// Launches outside the step: the 2D transform of omega into w_hat (after
+// the fields were set from outside), as a row pass and a column pass.
+enum { KIND_ROWFWD_OMEGA = 100, KIND_COLPASS_WINIT = 101 };
 
 struct LaunchCfg {
   int grid_x, grid_y;   // grid (the member index is the last grid dimension)
@@ -148,6 +173,9 @@ template <class T> int row_kernel_occupancy(int kind, int log2nx, int variant, i
 template <class T> int col_kernel_occupancy(int log2ny, int threads, size_t smem);
 template <class T> void set_row_smem_limits(int lim);
 template <class T> void set_col_smem_limits(int lim);
+// the column DFT of the low row modes of g (FP32 members): low_rows -> low_hat;
+// twff: W[k] = exp(2 pi i k / NMAX) as (cos hi, cos lo, sin hi, sin lo)
+void launch_lowmode_cols(const MemberDesc* d, int nmem, int log2ny, const float4* twff, cudaStream_t st);
 
 // ---- kernel launchers (step_kernels.cu / diag_kernels.cu) ----
 struct RowCfg {
@@ -170,6 +198,9 @@ template <class T> void launch_convert_out(const T* src, double* dst, long long 
 // non-finite count) of CTA b; returns the number of CTAs used
 template <class T> int launch_mass_partials(const T* f, long long count, double* out, int max_ctas,
                                             cudaStream_t st);
+// the partials folded on the device in a fixed order: out[0..2] = (sum,
+// compensation, non-finite count); one warp
+void launch_mass_fold(const double* partials, int ctas, double* out, cudaStream_t st);
 // structure factor: row transform of phi into xs (complex ny x nx/2), then per
 // partial sums per CTA of the structure-factor pass (see k_sf_cols)
 constexpr int kSfMoments = 7;

@@ -91,6 +91,46 @@ __device__ __forceinline__ void col_multiply_k(const ColConsts<T>& K, int m, T q
     }
   }
 }
+// FP32 inertial members: omega carried in 2D spectral form (w_hat).  At mode
+// (m, row nn): va = g_hat, vb = the transform of the advective increment A,
+// Wn = omega_hat^n (relabelled at a wrap).  omega* = Wn + A and Eq. forOmega
+// in increment form, omega^{n+1} = omega* + (dt g - 2 C omega*) / (1 + C),
+// C = dt nu k^2 / 2, then psi = omega^{n+1} / k^2.  Returns omega^{n+1}
+// (unnormalised, the new w_hat); va <- psi_hat norm, vb <- omega^{n+1} norm,
+// the inputs of the inverse column transforms.  Every mode is stored as its
+// own FP32 number from step to step, so each keeps its own relative
+// precision; the real omega of the stencils is derived from w_hat.
+__device__ __forceinline__ float2 col_multiply_wspec(const ColConsts<float>& K, int m, float qx, float sqx, int nn,
+                                                     float2& va, float2& vb, float2 Wn) {
+  const int ns = nn < (K.ny >> 1) ? nn : nn - K.ny;
+  const float ky = (float)ns * K.qyu - sqx;
+  const float k2 = qx * qx + ky * ky;
+  if (nn == (K.ny >> 1) || (m == 0 && nn == 0)) {     // Nyquist row and k = 0: omega = psi = 0
+    va = float2{0.f, 0.f};
+    vb = float2{0.f, 0.f};
+    return float2{0.f, 0.f};
+  }
+  const float2 G = va, A = vb;
+  const float2 Ws = float2{Wn.x + A.x, Wn.y + A.y};
+  const float cc = K.cnu * k2;
+  const float inv = quot(1.f, 1.f + cc);
+  const float2 W1 = float2{Ws.x + (K.dt * G.x - 2.f * cc * Ws.x) * inv, Ws.y + (K.dt * G.y - 2.f * cc * Ws.y) * inv};
+  const float ik = quot(K.norm, k2);
+  va = float2{W1.x * ik, W1.y * ik};
+  vb = float2{W1.x * K.norm, W1.y * K.norm};
+  return W1;
+}
+
+// FP32: g_hat at (m, row nn) from low_hat when the mode lies in the low window
+// (the force's transform there carries the rounding of the row transform's
+// compensated low modes only, see low_row_modes in step_rows.cu)
+__device__ __forceinline__ void low_override(const MemberDesc& D, int m, int nn, int ny, float2& v) {
+  if (m > D.lowm) return;
+  const int ns = nn < (ny >> 1) ? nn : nn - ny;
+  if (ns < -D.lown || ns > D.lown) return;
+  v = static_cast<const float2*>(D.low_hat)[m * (2 * D.lown + 1) + ns + D.lown];
+}
+
 // the same with the kind chosen at run time (mode 0 or 1, and K.stokes)
 template <class T>
 __device__ __forceinline__ void col_multiply(int mode, const ColConsts<T>& K, int m, T qx, T sqx, int nn,
@@ -175,27 +215,32 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_colpass(const MemberDesc
   cp_async_wait_all();
 }
 
-// The FP32 column pass body for one compile-time kind (0: phi; 1: inertial flow; 2:
-// Stokes flow), so no per-point branch on the mode or the member's regime.
+// The FP32 column pass body for one compile-time kind (0: phi; 1: inertial
+// flow with w_hat; 2: Stokes flow; 4: the forward column transform of omega's
+// row transform into w_hat), so no per-point branch on the mode or the
+// member's regime.
 template <int LN, int KIND>
 __device__ __forceinline__ void colpass_pair_body(const MemberDesc& D, int log2nx, const float2* __restrict__ tw,
                                                   unsigned char* smem_raw) {
   constexpr int log2ny = LN;
-  constexpr bool two = KIND != 2;                       // second input field
+  constexpr bool two = KIND == 0 || KIND == 1;          // second input field
   using T = float;
   using C = float2;
   const int nx = 1 << log2nx, ny = 1 << log2ny;
   const int Tc = ny >> kLogP;
   const int ipc = blockDim.x / Tc;
   const int inst = threadIdx.x / Tc, t = threadIdx.x - inst * Tc;
-  const int nitems = nx >> 2;
+  const int nitems = KIND == 4 && !D.wspec ? 0 : nx >> 2;
   const int stride = gridDim.x * ipc;
   unsigned char* base = smem_raw + (size_t)inst * colpass_inst_bytes(ny, sizeof(T));
   float4* st0 = reinterpret_cast<float4*>(base);
   float4* st1 = st0 + ny;
   float4* buf = st1 + ny;
-  float4* in0 = static_cast<float4*>(KIND == 0 ? D.xs_phi : D.xs_g);
+  float4* in0 = static_cast<float4*>(KIND == 0 ? D.xs_phi : (KIND == 4 ? D.xs_w : D.xs_g));
   float4* in1 = static_cast<float4*>(KIND == 0 ? D.xs_f : D.xs_w);
+  float4* what = static_cast<float4*>(D.w_hat);
+  // a wrap during the step relabels omega_hat^n: (m, n) <- (m, n + m dK)
+  const int dK = (KIND == 1 && D.remap) ? (int)(D.st->dK & (ny - 1)) : 0;
   float2* tws = reinterpret_cast<float2*>(smem_raw + (size_t)ipc * colpass_inst_bytes(ny, sizeof(T)));
   stage_tables_to_smem(tws, tw, log2ny, kLogP, threadIdx.x, blockDim.x);
 
@@ -235,13 +280,55 @@ __device__ __forceinline__ void colpass_pair_body(const MemberDesc& D, int log2n
     fft_reg2<false>(a0, b0, log2ny, t, buf, tws);
     if (two) fft_reg2<false>(a1, b1, log2ny, t, buf, tws);
     const int m0 = active ? 2 * cb : 0, m1 = m0 + 1;
+    if (KIND == 4) {                                    // omega's 2D transform: the new w_hat
+      if (active) {
+        float4* o = what + (size_t)cb * ny;
+#pragma unroll
+        for (int q = 0; q < kP; ++q) o[t + q * Tc] = make_float4(a0[q].x, a0[q].y, b0[q].x, b0[q].y);
+      }
+      continue;
+    }
+    if ((KIND == 1 || KIND == 2) && D.low && m0 <= D.lowm) {   // the force's low modes
+#pragma unroll
+      for (int q = 0; q < kP; ++q) {
+        low_override(D, m0, t + q * Tc, ny, a0[q]);
+        low_override(D, m1, t + q * Tc, ny, b0[q]);
+      }
+    }
     const double qa_d = m0 * K.qx_unit, qb_d = m1 * K.qx_unit;
     const T qa = (T)qa_d, qb = (T)qb_d;
     const T sqa = (T)(K.s_d * qa_d), sqb = (T)(K.s_d * qb_d);   // s q_x formed in double
+    if (KIND == 1) {
+      float4* wc = what + (size_t)(active ? cb : 0) * ny;
+      if (dK) {                                         // stage omega_hat^n so that rows can be relabelled
 #pragma unroll
-    for (int q = 0; q < kP; ++q) {
-      col_multiply_k<KIND>(K, m0, qa, sqa, t + q * Tc, a0[q], a1[q]);
-      col_multiply_k<KIND>(K, m1, qb, sqb, t + q * Tc, b0[q], b1[q]);
+        for (int q = 0; q < kP; ++q) buf[pad8(t + q * Tc)] = wc[t + q * Tc];
+        __syncthreads();
+      }
+#pragma unroll
+      for (int q = 0; q < kP; ++q) {
+        const int nn = t + q * Tc;
+        float2 Wa, Wb;
+        if (dK) {
+          const float4 xa = buf[pad8((nn + m0 * dK) & (ny - 1))], xb = buf[pad8((nn + m1 * dK) & (ny - 1))];
+          Wa = float2{xa.x, xa.y};
+          Wb = float2{xb.z, xb.w};
+        } else {
+          const float4 x = wc[nn];
+          Wa = float2{x.x, x.y};
+          Wb = float2{x.z, x.w};
+        }
+        const float2 Na = col_multiply_wspec(K, m0, qa, sqa, nn, a0[q], a1[q], Wa);
+        const float2 Nb = col_multiply_wspec(K, m1, qb, sqb, nn, b0[q], b1[q], Wb);
+        if (active) wc[nn] = make_float4(Na.x, Na.y, Nb.x, Nb.y);
+      }
+      if (dK) __syncthreads();                          // buf is the exchange buffer again
+    } else {
+#pragma unroll
+      for (int q = 0; q < kP; ++q) {
+        col_multiply_k<KIND>(K, m0, qa, sqa, t + q * Tc, a0[q], a1[q]);
+        col_multiply_k<KIND>(K, m1, qb, sqb, t + q * Tc, b0[q], b1[q]);
+      }
     }
     fft_reg2<true>(a0, b0, log2ny, t, buf, tws);
     if (active) {
@@ -259,6 +346,111 @@ __device__ __forceinline__ void colpass_pair_body(const MemberDesc& D, int log2n
     }
   }
   cp_async_wait_all();
+}
+
+// Error-free transformations in FP32 (Knuth's TwoSum; the product's error by
+// one fused multiply-add) for the double-float sums of k_lowmode_cols.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float ph, float pl) {
+  const float s = __fadd_rn(hi, ph);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(ph, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(e, pl));
+}
+// a (b_hi + b_lo) as hi + lo: the rounded product, its exact error and the
+// product with the low part
+__device__ __forceinline__ void ff_mul(float a, float bh, float bl, float& ph, float& pl) {
+  ph = __fmul_rn(a, bh);
+  pl = __fmaf_rn(a, bl, __fmaf_rn(a, bh, -ph));
+}
+
+// The column DFT of the low row modes of g (FP32 members):
+//   low_hat[m][n + lown] = sum_j low_rows[m][j] exp(-2 pi i n j / ny),
+// m <= lowm, |n| <= lown.  Each term is the product of an FP32 coefficient
+// with a double-float twiddle, formed without rounding error to about 2^-48,
+// and the four real sums (Re r cos, Im r sin, Im r cos, Re r sin) are
+// double-float sums (TwoSum), so the result carries essentially only the
+// rounding of the coefficients themselves.  A CTA holds two outputs; four
+// warps share one output's rows in quarters (lanes coalesced along j, four
+// rows in flight per lane); lanes and quarters are folded in a fixed order,
+// as float pairs.
+constexpr int kLowColsQuarters = 4;
+__global__ void __launch_bounds__(256) k_lowmode_cols(const MemberDesc* __restrict__ descs, int log2ny,
+                                                      const float4* __restrict__ twff) {
+  const MemberDesc& D = descs[blockIdx.y];
+  if (!D.low) return;                                  // uniform per CTA
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int o = blockIdx.x * 2 + (warp >> 2), qtr = warp & 3;
+  const int nn = 2 * D.lown + 1;
+  const bool has = o < (D.lowm + 1) * nn;
+  const int m = has ? o / nn : 0, ns = has ? o - m * nn - D.lown : 0;
+  const int ny = 1 << log2ny;
+  const int tshift = LOG2_NMAX - log2ny;
+  const int step = ns & (ny - 1);
+  const int rows = ny / kLowColsQuarters > 0 ? ny / kLowColsQuarters : 1;
+  const int j0 = qtr * rows, j1 = min(ny, j0 + rows);
+  const float2* lr = static_cast<const float2*>(D.low_rows) + ((size_t)m << log2ny);
+  float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
+  if (has) {
+    for (int jb = j0; jb < j1; jb += 128) {
+      float2 r[4];
+      float4 w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {                    // loads first: four rows in flight
+        const int j = jb + u * 32 + lane;
+        const bool in = j < j1;
+        r[u] = in ? lr[j] : float2{0.f, 0.f};
+        w[u] = in ? __ldg(twff + (((step * j) & (ny - 1)) << tshift)) : float4{1.f, 0.f, 0.f, 0.f};
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float ph, pl;
+        ff_mul(r[u].x, w[u].x, w[u].y, ph, pl);        // Re r cos
+        ff_add(h[0], l[0], ph, pl);
+        ff_mul(r[u].y, w[u].z, w[u].w, ph, pl);        // Im r sin
+        ff_add(h[1], l[1], ph, pl);
+        ff_mul(r[u].y, w[u].x, w[u].y, ph, pl);        // Im r cos
+        ff_add(h[2], l[2], ph, pl);
+        ff_mul(r[u].x, w[u].z, w[u].w, ph, pl);        // Re r sin
+        ff_add(h[3], l[3], ph, pl);
+      }
+    }
+  }
+  // fold the lanes pairwise in a fixed tree, every sum kept as a float pair
+  for (int off = 16; off > 0; off >>= 1) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float oh = __shfl_down_sync(0xffffffffu, h[k], off), ol = __shfl_down_sync(0xffffffffu, l[k], off);
+      if (lane < off) ff_add(h[k], l[k], oh, ol);
+    }
+  }
+  __shared__ float part[8][8];
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      part[warp][k] = h[k];
+      part[warp][4 + k] = l[k];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {                               // the four quarters in order
+    const int oo = blockIdx.x * 2 + threadIdx.x;
+    if (oo < (D.lowm + 1) * nn) {
+      float H[4] = {0.f, 0.f, 0.f, 0.f}, L[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int q = 0; q < kLowColsQuarters; ++q)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) ff_add(H[k], L[k], part[4 * threadIdx.x + q][k], part[4 * threadIdx.x + q][4 + k]);
+      // r conj(w): Re = Re r cos + Im r sin, Im = Im r cos - Re r sin
+      ff_add(H[0], L[0], H[1], L[1]);
+      ff_add(H[2], L[2], -H[3], -L[3]);
+      static_cast<float2*>(D.low_hat)[oo] = float2{__fadd_rn(H[0], L[0]), __fadd_rn(H[2], L[2])};
+    }
+  }
+}
+
+void launch_lowmode_cols(const MemberDesc* d, int nmem, int log2ny, const float4* twff, cudaStream_t st) {
+  const int outs = (kLowM + 1) * (2 * kLowN + 1);
+  k_lowmode_cols<<<dim3((outs + 1) / 2, nmem), 256, 0, st>>>(d, log2ny, twff);
 }
 
 // FP32 column pass over whole chunks: item cb = the two modes m = 2cb, 2cb+1,
@@ -285,6 +477,7 @@ const void* colpass_pair_fn(int kind) {
     case 0: return (const void*)k_colpass_pair<LN, 0>;
     case 1: return (const void*)k_colpass_pair<LN, 1>;
     case 2: return (const void*)k_colpass_pair<LN, 2>;
+    case 4: return (const void*)k_colpass_pair<LN, 4>;
     default: return (const void*)k_colpass_pair<LN, 3>;
   }
 }
@@ -298,12 +491,13 @@ void launch_col_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int 
   with_log2n(log2ny, [&](auto L) {
     constexpr int LN = decltype(L)::value;
     if constexpr (sizeof(T) == 4) {
-      // variant of the flow pass: 1 inertial members, 2 Stokes, 3 mixed
-      const int k = mode == 0 ? 0 : (c.variant >= 1 && c.variant <= 3 ? c.variant : 3);
+      // variant of the flow pass: 1 inertial members, 2 Stokes, 3 mixed; 4: seeding w_hat
+      const int k = kind == KIND_COLPASS_WINIT ? 4 : (mode == 0 ? 0 : (c.variant >= 1 && c.variant <= 3 ? c.variant : 3));
       switch (k) {
         case 0: k_colpass_pair<LN, 0><<<grid, c.threads, c.smem, st>>>(d, log2nx, tw); break;
         case 1: k_colpass_pair<LN, 1><<<grid, c.threads, c.smem, st>>>(d, log2nx, tw); break;
         case 2: k_colpass_pair<LN, 2><<<grid, c.threads, c.smem, st>>>(d, log2nx, tw); break;
+        case 4: k_colpass_pair<LN, 4><<<grid, c.threads, c.smem, st>>>(d, log2nx, tw); break;
         default: k_colpass_pair<LN, 3><<<grid, c.threads, c.smem, st>>>(d, log2nx, tw); break;
       }
     } else
@@ -330,7 +524,7 @@ void set_col_smem_limits(int lim) {
     with_log2n(ln, [&](auto L) {
       constexpr int LN = decltype(L)::value;
       if constexpr (sizeof(T) == 4) {
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < 5; ++k)
           cudaFuncSetAttribute(colpass_pair_fn<LN>(k), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
       } else
         cudaFuncSetAttribute(k_colpass<T, LN>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);

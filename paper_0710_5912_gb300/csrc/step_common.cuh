@@ -58,6 +58,17 @@ __device__ __forceinline__ void step_state_set(const MemberDesc& D, long long n)
 }
 
 
+// One step of Kahan's compensated summation: returns the new running sum of
+// s + x; c carries the excess of the additions so far (the exact sum is the
+// returned value minus c).  Explicit round-to-nearest operations keep the
+// compiler from simplifying it.
+__device__ __forceinline__ float kahan_add(float s, float x, float& c) {
+  const float y = __fsub_rn(x, c);
+  const float t = __fadd_rn(s, y);
+  c = __fsub_rn(__fsub_rn(t, s), y);
+  return t;
+}
+
 // ---- asynchronous global -> shared copies (cp.async; the wait is a hardware
 // instruction, not a spin loop)
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }

@@ -4,8 +4,10 @@
 //
 //   stencil1     item 1 + item 2's advection at s = s^n (Eq. advective with the
 //                Eq. p1y stencils): phi* = phi - dt J(psi, phi) and omega* =
-//                omega - dt J(psi, omega), real; omega* is written at the
-//                relabelled positions when the strain wraps during the step.
+//                omega - dt J(psi, omega), real (FP32 inertial members: the
+//                increment -dt J(psi, omega) alone, see step_cols.cu); omega*
+//                is written at the relabelled positions when the strain wraps
+//                during the step.
 //   rowfwd_phi   row (x) transforms of the phi*, f = phi^3 and omega* row
 //                pairs -> x-spectral buffers, plus each row's real Nyquist
 //                coefficient of phi* and omega*.
@@ -18,7 +20,9 @@
 //   stencil2     mu = -a phi + b phi^3 - kappa lap_c phi and the body-force curl
 //                F = d_x phi d_y mu - d_y phi d_x mu at s = s^{n+1} (Eq. G);
 //                g = -F/rho, or -F/eta for Stokes, real.
-//   rowfwd_g     row transforms of g row pairs.
+//   rowfwd_g     row transforms of g row pairs (FP32: plus the low row modes
+//                of g with compensated sums).
+//   lowmode      FP32: the column DFT of those low row modes.
 //   colpass_flow column transforms; Crank-Nicolson vorticity update in increment
 //                form omega^{n+1} = omega* + (1 - C/2)^-1 (C omega* + g) and the
 //                Poisson solve psi = omega / k^2 (items 2-3), or the Stokes solve
@@ -105,6 +109,33 @@ __device__ __forceinline__ void ldg2(const double* p, double& a, double& b) {
 __device__ __forceinline__ void st2(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
 __device__ __forceinline__ void st2(double* p, double a, double b) {
   *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+
+// The advective increment of omega alone, -dt (D_y psi D_x omega - D_x psi
+// D_y omega) (Eq. advective), written in place of omega* when omega is carried
+// in spectral form (MemberDesc::wspec).  One expression for the tile and the
+// streamed stencil, so both give the same bits.
+template <class T>
+__device__ __forceinline__ T advect_incr(T dt, T dyp, T dxf, T dxp, T dyf) {
+  return -(dt * (dyp * dxf - dxp * dyf));
+}
+
+// a b - c d with a single rounding of the result (Kahan's algorithm with two
+// fused multiply-adds): w = c d rounded, e = w - c d exactly, f = a b - w
+// rounded once, result f + e.  The body-force curl is a small difference of
+// two products of derivatives; this keeps its rounding relative to the result
+// instead of to the products.  Sign-symmetric, so phi -> -phi stays exact.
+__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
+  const float w = __fmul_rn(c, d);
+  const float e = __fmaf_rn(-c, d, w);
+  const float f = __fmaf_rn(a, b, -w);
+  return __fadd_rn(f, e);
+}
+__device__ __forceinline__ double diff_of_products(double a, double b, double c, double d) {
+  const double w = __dmul_rn(c, d);
+  const double e = __fma_rn(-c, d, w);
+  const double f = __fma_rn(a, b, -w);
+  return __dadd_rn(f, e);
 }
 
 // Eight reals of a tile row, cols c .. c+7 (c a multiple of 4): the stencil
@@ -235,8 +266,13 @@ __device__ __forceinline__ void stencil1_body(const MemberDesc& D, const T* tile
       T dxf[4], dyf[4];
       grad4<NEG>(ld8(t2 + (tr + 1) * W + 4 * q), C, ld8(t2 + (tr - 1) * W + 4 * q), sc.w0, sc.w1, inv2h, dxf, dyf);
       T r[4];
+      if (D.wspec) {
 #pragma unroll
-      for (int p = 0; p < 4; ++p) r[p] = C.v[p + 2] - dt * (dyp[p] * dxf[p] - dxp[p] * dyf[p]);
+        for (int p = 0; p < 4; ++p) r[p] = advect_incr(dt, dyp[p], dxf[p], dxp[p], dyf[p]);
+      } else {
+#pragma unroll
+        for (int p = 0; p < 4; ++p) r[p] = C.v[p + 2] - dt * (dyp[p] * dxf[p] - dxp[p] * dyf[p]);
+      }
       T* orow = oms + ((size_t)y << log2nx);
       if (!wrap) {
         st4(orow + x, r[0], r[1], r[2], r[3]);
@@ -332,7 +368,7 @@ __device__ __forceinline__ void stencil2_body(const MemberDesc& D, const T* tp, 
     grad4<NEG>(mU, mC, mD, sc.w0, sc.w1, inv2h, dxm, dym);
     T r[4];
 #pragma unroll
-    for (int p = 0; p < 4; ++p) r[p] = cf * (dxp[p] * dym[p] - dyp[p] * dxm[p]);
+    for (int p = 0; p < 4; ++p) r[p] = cf * diff_of_products(dxp[p], dym[p], dyp[p], dxm[p]);
     st4(gout + ((size_t)y << log2nx) + x, r[0], r[1], r[2], r[3]);
     pD = pC;
     pC = pU;
@@ -451,8 +487,13 @@ __device__ __forceinline__ void stencil1_stream_body(const MemberDesc& D, const 
       T dxf[4], dyf[4];
       grad4<NEG>(oU, oC, oD, sc.w0, sc.w1, inv2h, dxf, dyf);
       T r[4];
+      if (D.wspec) {
 #pragma unroll
-      for (int p = 0; p < 4; ++p) r[p] = oC.v[p + 2] - dt * (dyp[p] * dxf[p] - dxp[p] * dyf[p]);
+        for (int p = 0; p < 4; ++p) r[p] = advect_incr(dt, dyp[p], dxf[p], dxp[p], dyf[p]);
+      } else {
+#pragma unroll
+        for (int p = 0; p < 4; ++p) r[p] = oC.v[p + 2] - dt * (dyp[p] * dxf[p] - dxp[p] * dyf[p]);
+      }
       T* orow = oms + ((size_t)y << log2nx);
       if (!wrap) {
         st4(orow + x, r[0], r[1], r[2], r[3]);

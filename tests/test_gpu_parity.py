@@ -2,11 +2,15 @@
 
 Tolerances (relative L2 per field): FP64 <= 1e-10 and FP32 <= 2e-5 after 200
 steps from the same seeded state; single steps from rough random states
-FP64 <= 1e-11, FP32 <= 1e-5.  FP32 psi is held to an error model of FP32
-arithmetic instead (fp32_model.psi32_model_ratio): the inverse operator of its
-solve amplifies the FP32 rounding of the lowest modes of its right-hand side.
-Index work (the wrap remap, checkpoint resume, graph replay, ensemble batching,
-the phi -> -phi symmetry) is bit-exact.
+FP64 <= 1e-11, FP32 <= 1e-5.  Every field is held to these, FP32 psi of
+inertial runs included (the FP32 path carries omega in spectral form and
+takes the force's lowest modes from compensated sums for that).  FP32 psi of
+Stokes runs (rho = 0), psi_hat = g_hat / (eta k^4), is held to an error model
+of FP32 arithmetic instead (fp32_model.psi32_model_ratio): 1/k^4 amplifies the
+rounding of the FP32 force at the lowest modes beyond 2e-5 (the measured
+relative L2 is printed by the 200-step Stokes test).  Index work (the wrap
+remap, checkpoint resume, graph replay, ensemble batching, the phi -> -phi
+symmetry) is bit-exact.
 """
 import math
 import os
@@ -63,16 +67,17 @@ def rough_state(nx, ny, seed, inertial=True):
     return phi, psi, om
 
 
-def assert_close(got, want, tol, rho, what="", prec=FP64, s=0.0, dx=1.0):
-    """Relative L2 per field, except FP32 psi, which is held to the FP32 error
-    model of fp32_model.psi32_model_ratio (its plain relative L2 is limited by
-    the conditioning of the solve)."""
+def assert_close(got, want, tol, rho, what="", prec=FP64, s=0.0, dx=1.0, psi_model=False):
+    """Relative L2 per field, except FP32 psi of Stokes runs (or with
+    psi_model), which is held to the FP32 error model of
+    fp32_model.psi32_model_ratio (its plain relative L2 is limited by the
+    k^-4 conditioning of the Stokes solve)."""
     names = ("phi", "psi", "omega")
     for name, a, b in zip(names, got, want):
         if rho == 0 and name == "omega":
             assert np.abs(a).max() == 0.0
             continue
-        if name == "psi" and prec == FP32:
+        if name == "psi" and prec == FP32 and (rho == 0 or psi_model):
             q = psi32_model_ratio(a, b, s, dx, rho)
             assert q <= PSI32_MODEL_MAX, f"{what} psi: error/model {q:.2f} > {PSI32_MODEL_MAX} " \
                                          f"(rel L2 {rel_l2(a, b):.2e})"
@@ -179,18 +184,40 @@ def test_paper_geometry_1024x512_across_a_wrap(prec, rho):
     assert K1 == K0 + 1
     got = gpu_run(nx, ny, prec, p, fields, 28, 8)
     want = oracle_run(p, fields, 28, 8)
-    assert_close(got, want, TOL_1[prec] * 10, rho, f"1024x512 rho={rho}", prec, s_end, 1.0)
+    assert_close(got, want, TOL_200[prec], rho, f"1024x512 rho={rho}", prec, s_end, 1.0)
 
 
 @pytest.mark.parametrize("rho", [0.0, 0.1, 1.0])
 def test_config_1024_side_by_side(rho):
-    """1024x1024 FP32, eta = 1, gdot = 0.003, dt = 0.005: a few steps against the oracle."""
+    """1024x1024 FP32, eta = 1, gdot = 0.003, dt = 0.005: three steps from the
+    quench against the oracle.  psi is held to the FP32 error model here: three
+    steps in, its lowest modes have grown to only a small fraction of what they
+    reach after 200 steps, where the 2e-5 gate applies (test_config_1024_200_steps)."""
     nx = ny = 1024
     p = oracle.Params(a=1, b=1, kappa=1, M=1, eta=1, rho=rho, gdot=0.003, dt=0.005)
     fields = inputs.quench_state(nx, ny, 3)
     got = gpu_run(nx, ny, FP32, p, fields, 0, 3)
     want = oracle_run(p, fields, 0, 3)
-    assert_close(got, want, 1e-5, rho, f"1024^2 rho={rho}", FP32, oracle.strain(3, p.gdot, p.dt, nx, ny)[0])
+    print(f"1024^2 rho={rho} 3 steps psi: rel L2 {rel_l2(got[1], want[1]):.3e}")
+    assert_close(got, want, 1e-5, rho, f"1024^2 rho={rho}", FP32, oracle.strain(3, p.gdot, p.dt, nx, ny)[0],
+                 psi_model=True)
+
+
+@pytest.mark.parametrize("rho", [0.0, 0.1, 1.0])
+def test_config_1024_200_steps(rho):
+    """1024x1024 FP32, eta = 1, gdot = 0.003, dt = 0.005, from the seeded +-0.01
+    quench: 200 steps against the oracle at 2e-5 relative L2 per field (FP32
+    psi of the Stokes run against the FP32 error model; its plain relative L2
+    is printed)."""
+    nx = ny = 1024
+    p = oracle.Params(a=1, b=1, kappa=1, M=1, eta=1, rho=rho, gdot=0.003, dt=0.005)
+    fields = inputs.quench_state(nx, ny, 3)
+    got = gpu_run(nx, ny, FP32, p, fields, 0, 200)
+    want = oracle_run(p, fields, 0, 200)
+    for name, a, b in zip(("phi", "psi", "omega"), got, want):
+        print(f"1024^2 rho={rho} 200 steps {name}: rel L2 {rel_l2(a, b):.3e}")
+    assert_close(got, want, TOL_200[FP32], rho, f"1024^2 rho={rho} 200 steps", FP32,
+                 oracle.strain(200, p.gdot, p.dt, nx, ny)[0])
 
 
 def test_config_4096_inertial_full_size_step():
@@ -347,6 +374,15 @@ def test_checkpoint_errors(tmp_path):
         with pytest.raises(shf.ShfError) as e:
             g.load(path)
         assert e.value.code == shf.SHF_EINVAL
+    with shf.Grid(32, 32, 0.5, FP32) as g:          # same size and precision, another dx
+        g.set_params()
+        g.init_noise(2)
+        before = g.get_fields()
+        with pytest.raises(shf.ShfError) as e:
+            g.load(path)
+        assert e.value.code == shf.SHF_EINVAL
+        after = g.get_fields()
+        assert all(np.array_equal(a, b) for a, b in zip(before, after))
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
