@@ -42,8 +42,7 @@ FALLBACK_HBM_GBS = 6800.0
 # (4 B in FP32): fields read + fields written (an x-spectral field of nx/2
 # complex per row is one real per point)
 KERNEL_REALS_PER_POINT = {
-    "stencil1": 5,        # phi, psi, omega in; phi*, advective increment a of omega out
-    "rowfwd_phi": 6,      # phi*, phi, a in; phi*, f, a (x-spectral) out
+    "stage1": 7,          # phi, psi, omega in; phi* (real), phi*, f, a (x-spectral) out
     "colpass_phi": 3,     # phi*, f in; phi increment out
     "rowinv_phi": 3,      # increment, phi* in; phi out
     "stencil2": 2,        # phi in; g out
@@ -485,7 +484,7 @@ def main():
                 "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, **PARAMS, "seed": SEED, "amp": AMP,
                            "parallelism": f"replicas x{world}" if world > 1 else "single grid",
                            "l2": "state + scratch 576 MiB > L2 (129 MB): inputs larger than L2, no flush",
-                           "autotuned": {"rowfwd_phi_points": tuned[0][0], "rowfwd_g_points": tuned[0][1],
+                           "autotuned": {"stage1_points": tuned[0][0], "rowfwd_g_points": tuned[0][1],
                                          "stencil_rows": tuned[0][2]}},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e,
                 # nine step kernels per step plus the one state-seeding launch of the run

@@ -182,16 +182,18 @@ int shf_structure_factor(shf_grid* g, double* S_binned, int nbins, double moment
 int shf_gradient_tensor(shf_grid* g, double G[3], double lengths[2]);
 
 /* Pick, per size class, the launch variants that run fastest on this GPU:
- * each of the two forward row passes (of phi*, f, omega* and of g) with 8 or
- * 16 points per thread (radix-8 or radix-16 stages; FP32 only) and the
- * stencil tile height (16 or 32 rows).
+ * the fused stage-1 row pass (the stage-1 stencil with the row transforms of
+ * phi*, f, omega*) with 8 or 16 points per thread (radix-8 or radix-16
+ * stages; FP32 only) and the stage-2 stencil tile height (16 or 32 rows).
+ * The g row pass keeps 16 points in FP32 (its first stage yields the force's
+ * low modes).
  * Each candidate's kernels are timed on the grid's own buffers; only kernels
  * that write scratch buffers run, so the state (fields, step) is unchanged and
  * results stay within the parity tolerances (the variants round differently).
  * cache_path (nullable): a JSON file of earlier choices keyed by
  * "NXxNY:fp32|fp64:inertial|stokes|mixed"; keys found there are applied
  * without trials, new ones are added.  choices (nullable, nchoices ints):
- * receives (rowfwd_phi_points, rowfwd_g_points, stencil_rows) per size class,
+ * receives (stage1_points, rowfwd_g_points, stencil_rows) per size class,
  * in order of first appearance among the members.  Parameters must be set.  Not for member
  * views.  SHF_EIO if the cache cannot be written.  The paper has no
  * counterpart: this is a performance knob of the implementation. */

@@ -139,8 +139,8 @@ def shf_step(h, nsteps=1):
     _check(lib().shf_step(h, int(nsteps)), h, "shf_step")
 
 
-KERNEL_KINDS = ("stencil1", "rowfwd_phi", "colpass_phi", "rowinv_phi", "stencil2", "rowfwd_g", "lowmode",
-                "colpass_flow", "rowinv_flow")
+KERNEL_KINDS = ("stage1", "colpass_phi", "rowinv_phi", "stencil2", "rowfwd_g", "lowmode", "colpass_flow",
+                "rowinv_flow")
 
 
 def shf_profile_step(h, nsteps):
@@ -219,7 +219,7 @@ def shf_step_host_f32(h, nx, ny, nsteps, phi=None, psi=None, omega=None, out=Non
 
 def shf_autotune(h, cache_path=None, nclasses=8):
     """Tune the launch variants per size class; returns
-    [(rowfwd_phi_points, rowfwd_g_points, stencil_rows), ...]."""
+    [(stage1_points, rowfwd_g_points, stencil_rows), ...]."""
     out = (ctypes.c_int * (3 * nclasses))()
     path = None if cache_path is None else str(cache_path).encode()
     _check(lib().shf_autotune(h, path, out, 3 * nclasses), h, "shf_autotune")

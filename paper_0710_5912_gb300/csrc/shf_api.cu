@@ -178,7 +178,7 @@ int sm_count() {
 template <class T>
 LaunchCfg persistent_cfg(int kind, int nfft, int max_inst, int items, size_t inst_bytes, int nmem, int P = kP) {
   LaunchCfg c{};
-  const bool fwd = kind == KIND_ROWFWD_PHI || kind == KIND_ROWFWD_G;
+  const bool fwd = kind == KIND_STAGE1 || kind == KIND_ROWFWD_G;
   const bool rows = fwd || kind == KIND_ROWINV_PHI || kind == KIND_ROWINV_FLOW;
   const int cta = rows ? rowfwd_cta_threads(P) : 512;
   const int Tf = nfft / P;
@@ -202,20 +202,20 @@ LaunchCfg persistent_cfg(int kind, int nfft, int max_inst, int items, size_t ins
   return c;
 }
 
-// The tuning knobs of a size class: points per thread of the forward row
-// transforms of phi and of g (8 or 16 each; FP64: 8) and the stencil tile
-// height (16 or 32, at most ny).  Zero means "the default".
+// The tuning knobs of a size class: points per thread of the fused stage-1
+// row pass (8 or 16; FP64: 8), of the g row pass (FP32: 16, whose radix-16
+// first stage yields the force's low modes; FP64: 8) and the stage-2 stencil
+// tile height (16 or 32, at most ny).  Zero means "the default".
 struct Tune {
-  int rowfwd_phi_points = 0;
+  int stage1_points = 0;
   int rowfwd_g_points = 0;
   int stencil_rows = 0;
 };
 
 template <class T>
 Tune resolved(const SizeClass& cl, Tune t) {
-  if (t.rowfwd_phi_points == 0 || sizeof(T) == 8) t.rowfwd_phi_points = rowfwd_default_points<T>();
-  // FP32: the g row pass takes the force's low modes from its radix-16 first stage
-  if (t.rowfwd_g_points == 0 || sizeof(T) == 8 || sizeof(T) == 4) t.rowfwd_g_points = rowfwd_default_points<T>();
+  if (t.stage1_points == 0 || sizeof(T) == 8) t.stage1_points = rowfwd_default_points<T>();
+  t.rowfwd_g_points = rowfwd_default_points<T>();
   const int maxrows = cl.ny < 32 ? cl.ny : 32;
   if (t.stencil_rows == 0 || t.stencil_rows > maxrows) t.stencil_rows = maxrows;
   return t;
@@ -226,32 +226,17 @@ void configure_class_t(SizeClass& cl, Tune tune) {
   tune = resolved<T>(cl, tune);
   const size_t R = sizeof(T), Cx = 2 * R;
   const int nx = cl.nx, ny = cl.ny, nmem = (int)cl.members.size();
-  // stencil tiles of TX = min(nx, 128) by TY rows, 4 x 4 outputs per thread
+  // stage-2 stencil tiles of TX = min(nx, 128) by TY rows, 4 x 4 outputs per thread
   const int TX = nx < 128 ? nx : 128, TY = tune.stencil_rows;
   LaunchCfg st{};
   st.grid_x = nx / TX;
   st.grid_y = ny / TY;
   st.threads = (TX / 4) * (TY / 4);
   st.variant = TY;
-  st.smem = stencil1_smem_bytes(TX, TY, R);
-  cl.cfg[KIND_STENCIL1] = st;
-  if (R == 4 && nx >= 128) {
-    // streamed stage-1 stencil: one CTA per resident slot, each warp a strip of
-    // at least four rows
-    LaunchCfg s1{};
-    s1.grid_x = nx / 128;
-    int gy = stencil1_stream_occupancy() * sm_count() / (s1.grid_x * (nmem > 0 ? nmem : 1));
-    const int gmax = ny / 16 > 1 ? ny / 16 : 1;
-    s1.grid_y = gy < 1 ? 1 : (gy > gmax ? gmax : gy);
-    s1.threads = 128;
-    s1.smem = 0;
-    s1.variant = kStencilStream;
-    cl.cfg[KIND_STENCIL1] = s1;
-  }
   st.smem = stencil2_smem_bytes(TX, TY, R);
   cl.cfg[KIND_STENCIL2] = st;
-  cl.cfg[KIND_ROWFWD_PHI] = persistent_cfg<T>(KIND_ROWFWD_PHI, nx, ny / 2, 3 * (ny / 2), rowfwd_inst_bytes(nx, R),
-                                               nmem, tune.rowfwd_phi_points);
+  cl.cfg[KIND_STAGE1] = persistent_cfg<T>(KIND_STAGE1, nx, ny / 2, ny / 2, 2 * stage1_inst_bytes(nx, R), nmem,
+                                           tune.stage1_points);
   cl.cfg[KIND_ROWFWD_G] = persistent_cfg<T>(KIND_ROWFWD_G, nx, ny / 2, ny / 2, rowfwd_inst_bytes(nx, R), nmem,
                                              tune.rowfwd_g_points);
   // column items: whole 16-byte chunks (two modes in FP32, one in FP64)
@@ -788,7 +773,7 @@ std::string tune_key(const shf_grid* o, const SizeClass& cl) {
 }
 
 // cache file: a JSON object, one entry per line:
-//   "NXxNY:fp32:inertial": {"rowfwd_phi_points": 16, "rowfwd_g_points": 8, "stencil_rows": 32},
+//   "NXxNY:fp32:inertial": {"stage1_points": 16, "rowfwd_g_points": 16, "stencil_rows": 32},
 std::map<std::string, Tune> read_tune_cache(const char* path) {
   std::map<std::string, Tune> m;
   if (!path) return m;
@@ -798,8 +783,8 @@ std::map<std::string, Tune> read_tune_cache(const char* path) {
   while (std::fgets(line, sizeof(line), f)) {
     char key[256];
     Tune t;
-    if (std::sscanf(line, " \"%255[^\"]\": {\"rowfwd_phi_points\": %d, \"rowfwd_g_points\": %d, \"stencil_rows\": %d",
-                    key, &t.rowfwd_phi_points, &t.rowfwd_g_points, &t.stencil_rows) == 4)
+    if (std::sscanf(line, " \"%255[^\"]\": {\"stage1_points\": %d, \"rowfwd_g_points\": %d, \"stencil_rows\": %d",
+                    key, &t.stage1_points, &t.rowfwd_g_points, &t.stencil_rows) == 4)
       m[key] = t;
   }
   std::fclose(f);
@@ -812,8 +797,8 @@ bool write_tune_cache(const char* path, const std::map<std::string, Tune>& m) {
   std::fprintf(f, "{\n");
   size_t i = 0;
   for (const auto& kv : m) {
-    std::fprintf(f, "  \"%s\": {\"rowfwd_phi_points\": %d, \"rowfwd_g_points\": %d, \"stencil_rows\": %d}%s\n",
-                 kv.first.c_str(), kv.second.rowfwd_phi_points, kv.second.rowfwd_g_points, kv.second.stencil_rows,
+    std::fprintf(f, "  \"%s\": {\"stage1_points\": %d, \"rowfwd_g_points\": %d, \"stencil_rows\": %d}%s\n",
+                 kv.first.c_str(), kv.second.stage1_points, kv.second.rowfwd_g_points, kv.second.stencil_rows,
                  ++i < m.size() ? "," : "");
   }
   std::fprintf(f, "}\n");
@@ -845,37 +830,37 @@ int time_kinds(shf_grid* o, SizeClass& cl, const int* kinds, int nk, float* ms) 
 }
 
 // Time the candidate values of each knob on the class's own buffers.  Only
-// kinds that write scratch (stencils: phi*, omega*, g; forward rows: the
-// x-spectral buffers) run, so the state (phi, psi, omega, step) is untouched.
+// kinds that write scratch (the stage-1 pass: phi*, omega*, the x-spectral
+// buffers; the stage-2 stencil: g) run, so the state (phi, psi, omega,
+// omega_hat, step) is untouched.
 template <class T>
 int tune_class(shf_grid* o, SizeClass& cl, Tune* best) {
   Tune t = resolved<T>(cl, Tune{});
-  if (sizeof(T) == 4) {
-    for (int kind : {KIND_ROWFWD_PHI, KIND_ROWFWD_G}) {   // the two forward passes tuned separately
-      float bestms = 0.f;
-      for (int P : {8, 16}) {
-        Tune c = t;
-        (kind == KIND_ROWFWD_PHI ? c.rowfwd_phi_points : c.rowfwd_g_points) = P;
-        configure_class_t<T>(cl, c);
-        float ms = 0.f;
-        const int rc = time_kinds<T>(o, cl, &kind, 1, &ms);
-        if (rc) return rc;
-        if (P == 8 || ms < bestms) {
-          bestms = ms;
-          (kind == KIND_ROWFWD_PHI ? t.rowfwd_phi_points : t.rowfwd_g_points) = P;
-        }
+  if (sizeof(T) == 4) {                                // the fused stage-1 row pass: 8 or 16 points
+    const int kind = KIND_STAGE1;
+    float bestms = 0.f;
+    for (int P : {8, 16}) {
+      Tune c = t;
+      c.stage1_points = P;
+      configure_class_t<T>(cl, c);
+      float ms = 0.f;
+      const int rc = time_kinds<T>(o, cl, &kind, 1, &ms);
+      if (rc) return rc;
+      if (P == 8 || ms < bestms) {
+        bestms = ms;
+        t.stage1_points = P;
       }
     }
   }
   if (cl.ny >= 32) {
-    const int st[2] = {KIND_STENCIL1, KIND_STENCIL2};
+    const int st[1] = {KIND_STENCIL2};
     float bestms = 0.f;
     for (int TY : {16, 32}) {
       Tune c = t;
       c.stencil_rows = TY;
       configure_class_t<T>(cl, c);
       float ms = 0.f;
-      const int rc = time_kinds<T>(o, cl, st, 2, &ms);
+      const int rc = time_kinds<T>(o, cl, st, 1, &ms);
       if (rc) return rc;
       if (TY == 16 || ms < bestms) {
         bestms = ms;
@@ -1320,7 +1305,7 @@ int shf_autotune(shf_grid* g, const char* cache_path, int* choices, int nchoices
     if (g->precision == SHF_FP64) t = resolved<double>(cl, t);
     else t = resolved<float>(cl, t);
     if ((int)(3 * c + 2) < nchoices) {
-      choices[3 * c] = t.rowfwd_phi_points;
+      choices[3 * c] = t.stage1_points;
       choices[3 * c + 1] = t.rowfwd_g_points;
       choices[3 * c + 2] = t.stencil_rows;
     }

@@ -92,12 +92,8 @@ __device__ __forceinline__ void strain_dev(long long n, double gdot, double dt, 
 // one x-spectral chunk column of each input field plus the buffer; rowinv
 // stages the 32-byte chunks of a row pair (nx complex) plus the buffer.
 __host__ __device__ constexpr size_t round128(size_t b) { return (b + 127) & ~(size_t)127; }
-// Stencil tiles (dynamic shared memory): stage 1 holds three (TY + 2) x
-// (TX + 4) tiles (phi, psi, omega); stage 2 a (TY + 4) x (TX + 12) phi tile
-// and a (TY + 2) x (TX + 12) mu tile.
-__host__ __device__ constexpr size_t stencil1_smem_bytes(int TX, int TY, size_t real_bytes) {
-  return 3 * (size_t)(TY + 2) * (TX + 4) * real_bytes;
-}
+// Stage-2 stencil tiles (dynamic shared memory): a (TY + 4) x (TX + 12) phi
+// tile and a (TY + 2) x (TX + 12) mu tile.
 __host__ __device__ constexpr size_t stencil2_smem_bytes(int TX, int TY, size_t real_bytes) {
   return (size_t)(2 * TY + 6) * (TX + 12) * real_bytes;
 }
@@ -111,6 +107,12 @@ __host__ __device__ constexpr size_t rowfwd_inst_bytes(int nx, size_t real_bytes
 __host__ __device__ constexpr size_t colpass_inst_bytes(int ny, size_t /*real_bytes*/) {
   return round128((2 * (size_t)ny + (size_t)padded_len8(ny)) * 16);
 }
+// the fused stage-1 row pass: per instance two padded buffers (phi*'s pair
+// and omega*'s), each holding a row pair's stencil outputs (2 nx reals) and
+// then serving as the FFT exchange buffer; stage1_inst_bytes is one buffer
+__host__ __device__ constexpr size_t stage1_inst_bytes(int nx, size_t real_bytes) {
+  return round128((size_t)padded_len(nx) * 2 * real_bytes);
+}
 __host__ __device__ constexpr size_t rowinv_inst_bytes(int nx, size_t real_bytes) {
   return round128(((size_t)nx + (size_t)padded_len(nx)) * 2 * real_bytes);
 }
@@ -122,10 +124,11 @@ __host__ __device__ constexpr size_t stage_table_bytes(int log2n, int LP, size_t
 
 // Row transforms come in two variants, P = 8 points per thread (radix-8
 // stages, 512-thread CTAs) and P = 16 (radix-16 stages, 256-thread CTAs, FP32
-// only); the column passes use 8 points and 512 threads.  The forward rows'
-// P and the stencil tile height are tuning knobs (shf_autotune); the FP32
-// inverse rows use P = 16 (8% faster than 8 in the flow pass, equal in the
-// phi pass at 4096^2).
+// only); the column passes use 8 points and 512 threads.  The fused stage-1
+// pass's P and the stage-2 stencil tile height are tuning knobs
+// (shf_autotune); the FP32 g row pass uses P = 16 (its first radix-16 stage
+// yields the force's low modes) and the FP32 inverse rows P = 16 (8% faster
+// than 8 in the flow pass, equal in the phi pass at 4096^2).
 constexpr int rowfwd_cta_threads(int P) { return P == 16 ? 256 : 512; }
 template <class T> constexpr int rowfwd_min_ctas(int P) { return P == 16 ? 3 : (sizeof(T) == 4 ? 2 : 1); }
 template <class T> constexpr int rowfwd_default_points() { return sizeof(T) == 4 ? 16 : 8; }
@@ -133,16 +136,15 @@ template <class T> constexpr int rowinv_default_points() { return sizeof(T) == 4
 
 // The launches of a step, in order (KIND_LOWMODE runs for FP32 classes only).
 enum StepKind {
-  KIND_STENCIL1 = 0,
-  KIND_ROWFWD_PHI = 1,
-  KIND_COLPASS_PHI = 2,
-  KIND_ROWINV_PHI = 3,
-  KIND_STENCIL2 = 4,
-  KIND_ROWFWD_G = 5,
-  KIND_LOWMODE = 6,
-  KIND_COLPASS_FLOW = 7,
-  KIND_ROWINV_FLOW = 8,
-  KIND_COUNT = 9
+  KIND_STAGE1 = 0,        // stage-1 stencil fused with the row transforms of phi*, f, omega*
+  KIND_COLPASS_PHI = 1,
+  KIND_ROWINV_PHI = 2,
+  KIND_STENCIL2 = 3,
+  KIND_ROWFWD_G = 4,
+  KIND_LOWMODE = 5,
+  KIND_COLPASS_FLOW = 6,
+  KIND_ROWINV_FLOW = 7,
+  KIND_COUNT = 8
 };
 // Launches outside the step: the 2D transform of omega into w_hat (after
 // the fields were set from outside), as a row pass and a column pass.
@@ -153,13 +155,9 @@ struct LaunchCfg {
   int threads;
   size_t smem;          // dynamic shared memory bytes
   int inst_per_cta;     // transform instances per CTA (persistent kinds)
-  int variant;          // rows: points per thread (8, 16); stencils: tile rows (16, 32);
+  int variant;          // rows: points per thread (8, 16); stage-2 stencil: tile rows (16, 32);
                         // FP32 flow column pass: members' regime (1 inertial, 2 Stokes, 3 mixed)
-                        // or kStencilStream (stage 1, FP32, nx >= 128)
 };
-constexpr int kStencilStream = 1;
-// resident CTAs per SM of the streamed stage-1 stencil (128 threads, no shared memory)
-int stencil1_stream_occupancy();
 
 template <class T> void launch_step_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int log2ny,
                                            const cplx<T>* tw, const LaunchCfg& c, cudaStream_t st);

@@ -69,6 +69,127 @@ __device__ __forceinline__ float kahan_add(float s, float x, float& c) {
   return t;
 }
 
+// ---------------------------------------------------------------- stencils
+// four consecutive reals at a 16-byte-aligned address
+template <class T>
+struct Quad {
+  T v[4];
+};
+__device__ __forceinline__ Quad<float> ld4(const float* p) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  return Quad<float>{{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ Quad<double> ld4(const double* p) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  return Quad<double>{{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ Quad<float> ldg4(const float* p) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  return Quad<float>{{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ Quad<double> ldg4(const double* p) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p)), b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  return Quad<double>{{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st4(float* p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void st4(double* p, double a, double b, double c, double d) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+  reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
+}
+// two reals at an address aligned to two elements
+__device__ __forceinline__ void ldg2(const float* p, float& a, float& b) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  a = v.x;
+  b = v.y;
+}
+__device__ __forceinline__ void ldg2(const double* p, double& a, double& b) {
+  const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+  a = v.x;
+  b = v.y;
+}
+__device__ __forceinline__ void st2(float* p, float a, float b) { *reinterpret_cast<float2*>(p) = make_float2(a, b); }
+__device__ __forceinline__ void st2(double* p, double a, double b) {
+  *reinterpret_cast<double2*>(p) = make_double2(a, b);
+}
+
+// The advective increment of omega alone, -dt (D_y psi D_x omega - D_x psi
+// D_y omega) (Eq. advective), written in place of omega* when omega is carried
+// in spectral form (MemberDesc::wspec).  One expression for the tile and the
+// streamed stencil, so both give the same bits.
+template <class T>
+__device__ __forceinline__ T advect_incr(T dt, T dyp, T dxf, T dxp, T dyf) {
+  return -(dt * (dyp * dxf - dxp * dyf));
+}
+
+// a b - c d with a single rounding of the result (Kahan's algorithm with two
+// fused multiply-adds): w = c d rounded, e = w - c d exactly, f = a b - w
+// rounded once, result f + e.  The body-force curl is a small difference of
+// two products of derivatives; this keeps its rounding relative to the result
+// instead of to the products.  Sign-symmetric, so phi -> -phi stays exact.
+__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
+  const float w = __fmul_rn(c, d);
+  const float e = __fmaf_rn(-c, d, w);
+  const float f = __fmaf_rn(a, b, -w);
+  return __fadd_rn(f, e);
+}
+__device__ __forceinline__ double diff_of_products(double a, double b, double c, double d) {
+  const double w = __dmul_rn(c, d);
+  const double e = __fma_rn(-c, d, w);
+  const double f = __fma_rn(a, b, -w);
+  return __dadd_rn(f, e);
+}
+
+// Eight reals of a tile row, cols c .. c+7 (c a multiple of 4): the stencil
+// row of a 4-point block whose first point sits at c + 2.
+template <class T>
+struct Row8 {
+  T v[8];
+};
+template <class T>
+__device__ __forceinline__ Row8<T> ld8(const T* p) {
+  const Quad<T> a = ld4(p), b = ld4(p + 4);
+  return Row8<T>{{a.v[0], a.v[1], a.v[2], a.v[3], b.v[0], b.v[1], b.v[2], b.v[3]}};
+}
+
+// Six reals of a tile row, cols c - 1 .. c + 4 (c a multiple of 4), read as
+// pairs at c - 2 and c + 4 and a quad at c: the stencil row of a 4-point
+// block of second differences whose first point sits at c.
+template <class T>
+struct Six {
+  T v[6];
+};
+__device__ __forceinline__ Six<float> ld6(const float* p) {
+  const float2 l = *reinterpret_cast<const float2*>(p - 2);
+  const float4 m = *reinterpret_cast<const float4*>(p);
+  const float2 r = *reinterpret_cast<const float2*>(p + 4);
+  return Six<float>{{l.y, m.x, m.y, m.z, m.w, r.x}};
+}
+__device__ __forceinline__ Six<double> ld6(const double* p) {
+  const double2 l = *reinterpret_cast<const double2*>(p - 2);
+  const double2 m0 = reinterpret_cast<const double2*>(p)[0], m1 = reinterpret_cast<const double2*>(p)[1];
+  const double2 r = *reinterpret_cast<const double2*>(p + 4);
+  return Six<double>{{l.y, m0.x, m0.y, m1.x, m1.y, r.x}};
+}
+
+// Derivatives at the 4 points (centre index p + 2) of rows U (j+1), C (j),
+// Dn (j-1): D_x f = (f(i+1) - f(i-1)) / 2h and Eq. p1y's sheared D_y^s f =
+// [w0 (f(i, j+1) - f(i, j-1)) + w1 (f(i+d, j+1) - f(i-d, j-1))] / 2h, with
+// d = -2 for s >= 0 (NEG = false) and d = +2 for s < 0 (NEG = true).
+template <bool NEG, class T>
+__device__ __forceinline__ void grad4(const Row8<T>& U, const Row8<T>& C, const Row8<T>& Dn, T w0, T w1, T inv2h,
+                                      T (&dx)[4], T (&dy)[4]) {
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    dx[p] = (C.v[p + 3] - C.v[p + 1]) * inv2h;
+    const T up = NEG ? U.v[p + 4] : U.v[p];         // f(i+d, j+1)
+    const T dn = NEG ? Dn.v[p] : Dn.v[p + 4];       // f(i-d, j-1)
+    dy[p] = (w0 * (U.v[p + 2] - Dn.v[p + 2]) + w1 * (up - dn)) * inv2h;
+  }
+}
+
+
 // ---- asynchronous global -> shared copies (cp.async; the wait is a hardware
 // instruction, not a spin loop)
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }

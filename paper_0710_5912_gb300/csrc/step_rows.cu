@@ -131,14 +131,12 @@ __device__ __forceinline__ void low_row_reduce(float* Zb, int t, const MemberDes
 }
 
 // ====================================================== forward row transforms
-// Work items: mode 0 (phi): per row pair p = rows (2p, 2p+1), item 0 = phi*,
-// item 1 = f = phi^3, item 2 = omega* (inertial members; with w_hat, the
-// advective increment of omega); mode 1 (g): one item per row pair, plus the
-// low row modes of g (FP32, P = 16); mode 2: omega's row pairs into xs_w (the
-// row half of the transform that seeds w_hat).  Each item stages the two real
-// rows (a, b) in shared memory and transforms a + i b (for f the staged phi
-// rows are cubed on the fly), so every output chunk of the pair is one whole
-// 32-byte piece.
+// Work items: one per row pair p = rows (2p, 2p+1); mode 1: g -> xs_g, plus
+// the low row modes of g (FP32, P = 16); mode 2: omega -> xs_w (the row half
+// of the transform that seeds w_hat).  Each item stages the two real rows
+// (a, b) in shared memory and transforms a + i b, so every output chunk of
+// the pair is one whole 32-byte piece.  (Stage 1's row transforms are fused
+// with its stencil: k_stage1_rows.)
 template <class T, int LN, int P, int MODE>
 __global__ void __launch_bounds__(rowfwd_cta_threads(P), rowfwd_min_ctas<T>(P)) k_rowfwd(const MemberDesc* __restrict__ descs, int log2ny,
                                                                const cplx<T>* __restrict__ tw) {
@@ -152,37 +150,20 @@ __global__ void __launch_bounds__(rowfwd_cta_threads(P), rowfwd_min_ctas<T>(P)) 
   const int Tf = nx / P;
   const int ipc = blockDim.x / Tf;
   const int inst = threadIdx.x / Tf, t = threadIdx.x - inst * Tf;
-  const int nsub = mode == 0 ? (D.stokes ? 2 : 3) : 1;
-  const int nitems = mode == 2 && !D.wspec ? 0 : (ny >> 1) * nsub;
+  const int nitems = mode == 2 && !D.wspec ? 0 : ny >> 1;
   const int stride = gridDim.x * ipc;
   unsigned char* base = smem_raw + (size_t)inst * rowfwd_inst_bytes(nx, sizeof(T));
   T* stage = reinterpret_cast<T*>(base);
   C* Z = reinterpret_cast<C*>(base + 2 * (size_t)nx * sizeof(T));
-  const T* phis = static_cast<const T*>(D.phi_star);
-  const T* phi = static_cast<const T*>(D.phi);
-  const T* oms = static_cast<const T*>(D.omega_star);
-  const T* gb = static_cast<const T*>(D.gbuf);
+  const T* src = mode == 1 ? static_cast<const T*>(D.gbuf) : static_cast<const T*>(D.omega);
   C* tws = reinterpret_cast<C*>(smem_raw + (size_t)ipc * rowfwd_inst_bytes(nx, sizeof(T)));
   stage_tables_to_smem(tws, tw, log2nx, log2_points<P>(), threadIdx.x, blockDim.x);
 
   auto issue = [&](int w) {
     if (w < nitems) {
-      const int p = w / nsub, sub = w - p * nsub;
-      const T *ra, *rb;
-      if (mode >= 1) {
-        const T* src = mode == 1 ? gb : static_cast<const T*>(D.omega);
-        ra = src + ((size_t)(2 * p) << log2nx);
-        rb = src + ((size_t)(2 * p + 1) << log2nx);
-      } else if (sub < 2) {
-        const T* src = sub == 0 ? phis : phi;             // phi* pair, or phi pair (cubed on the fly)
-        ra = src + ((size_t)(2 * p) << log2nx);
-        rb = src + ((size_t)(2 * p + 1) << log2nx);
-      } else {
-        ra = oms + ((size_t)(2 * p) << log2nx);
-        rb = oms + ((size_t)(2 * p + 1) << log2nx);
-      }
+      const T* ra = src + ((size_t)(2 * w) << log2nx);
       copy_async(stage, ra, nx * (int)sizeof(T), t, Tf);
-      copy_async(stage + nx, rb, nx * (int)sizeof(T), t, Tf);
+      copy_async(stage + nx, ra + nx, nx * (int)sizeof(T), t, Tf);
     }
     cp_async_commit();
   };
@@ -192,8 +173,7 @@ __global__ void __launch_bounds__(rowfwd_cta_threads(P), rowfwd_min_ctas<T>(P)) 
   issue(w);
   for (int it = 0; it < iters; ++it, w += stride) {
     const bool active = w < nitems;
-    const int p = w / nsub, sub = w - p * nsub;
-    const bool cube = mode == 0 && sub == 1;
+    const int p = w;
     cp_async_wait_all();
     __syncthreads();
     if constexpr (sizeof(T) == 4 && P == 16 && MODE == 1) {   // the force's low row modes, part 1
@@ -203,8 +183,7 @@ __global__ void __launch_bounds__(rowfwd_cta_threads(P), rowfwd_min_ctas<T>(P)) 
 #pragma unroll
     for (int q = 0; q < P; ++q) {
       const int i = t + q * Tf;
-      const T a = stage[i], bb = stage[nx + i];
-      v[q] = cube ? C{(a * a) * a, (bb * bb) * bb} : C{a, bb};
+      v[q] = C{stage[i], stage[nx + i]};
     }
     __syncthreads();                                    // stage free
     issue(w + stride);                                  // next item streams in during the transform
@@ -213,28 +192,217 @@ __global__ void __launch_bounds__(rowfwd_cta_threads(P), rowfwd_min_ctas<T>(P)) 
     }
     fft_reg<false>(v, log2nx, t, Z, tws);
     reg_to_smem(v, log2nx, t, Z);
-    if (active) {
-      if (mode >= 1) {
-        write_pair_rows<LC>(Z, static_cast<C*>(mode == 1 ? D.xs_g : D.xs_w), 2 * p, nx, ny, t, Tf);
-      } else if (sub < 2) {
-        write_pair_rows<LC>(Z, static_cast<C*>(sub == 0 ? D.xs_phi : D.xs_f), 2 * p, nx, ny, t, Tf);
-        if (sub == 0 && t == 0) {                        // phi*'s row Nyquist coefficients
-          const C zn = Z[pad16(nx >> 1)];
-          static_cast<T*>(D.nyq_phi)[2 * p] = zn.x;
-          static_cast<T*>(D.nyq_phi)[2 * p + 1] = zn.y;
-        }
-      } else {
-        write_pair_rows<LC>(Z, static_cast<C*>(D.xs_w), 2 * p, nx, ny, t, Tf);
-        if (t == 0) {
-          const C zn = Z[pad16(nx >> 1)];
-          static_cast<T*>(D.nyq_omega)[2 * p] = zn.x;
-          static_cast<T*>(D.nyq_omega)[2 * p + 1] = zn.y;
-        }
-      }
-    }
+    if (active) write_pair_rows<LC>(Z, static_cast<C*>(mode == 1 ? D.xs_g : D.xs_w), 2 * p, nx, ny, t, Tf);
     __syncthreads();                                    // Z reads done before the next transform
   }
   cp_async_wait_all();
+}
+
+// ===================================== stage 1 fused with its row transforms
+// Per row pair p (rows j0 = 2p, j1 = 2p + 1), item 1 + item 2's advection at
+// s = s^n (Eq. advective with the Eq. p1y stencils) and the row transforms
+// of what it makes, with no HBM round trip in between:
+//   phi* = phi - dt J(psi, phi): written out (the base of phi's increment)
+//     and row-transformed -> xs_phi, nyq_phi;
+//   f = phi^3 (the pre-advection phi) -> xs_f;
+//   inertial members: omega* = omega - dt J(psi, omega) (written out, the base
+//     of omega's increment) -> xs_w, nyq_omega; or, with w_hat, the increment
+//     a = -dt J(psi, omega) alone -> xs_w.  At a wrap these are taken at the
+//     relabelled positions (row j shifted by the wrap's cells).
+// One stencil pass per item reads the four rows j0 - 1 .. j1 + 1 of phi, psi
+// and omega straight from global memory (the halo rows come from L2), a
+// thread making 4 x 2 outputs of each field per column group of 4, and writes
+// the two pairs into the instance's two padded buffers; each buffer then feeds
+// the register FFT and serves as its exchange buffer.  The next item's rows
+// are prefetched into L2 while the current one is transformed.
+
+// columns x0 - 2 .. x0 + 5 of a global row (x0 a multiple of 4), periodic
+template <class T>
+__device__ __forceinline__ Row8<T> ld8_row(const T* row, int x0, int mx) {
+  T l0, l1, r0, r1;
+  ldg2(row + ((x0 - 2) & mx), l0, l1);
+  const Quad<T> q = ldg4(row + x0);
+  ldg2(row + ((x0 + 4) & mx), r0, r1);
+  return Row8<T>{{l0, l1, q.v[0], q.v[1], q.v[2], q.v[3], r0, r1}};
+}
+
+// the stencils of both rows of the pair, both fields in one pass over their
+// inputs (psi's derivatives shared): bufp <- phi* = phi - dt J(psi, phi)
+// (also to gphi when not null); inertial: bufw <- omega - dt J(psi, omega),
+// or the increment alone (INCR), at the rows' relabelling cells sh0, sh1
+// (also to gom when not null)
+template <bool NEG, bool INCR, bool OMEGA, class T>
+__device__ __forceinline__ void stage1_pair(const T* phi, const T* psi, const T* om, T* bufp, T* bufw, T* gphi,
+                                            T* gom, int j0, int log2nx, int my, const Shear<T>& sc, T dt,
+                                            T inv2h, int t, int Tf, int sh0, int sh1) {
+  const int nx = 1 << log2nx, mx = nx - 1;
+  auto row = [&](const T* a, int j) { return a + ((size_t)(j & my) << log2nx); };
+  for (int k = t; k < (nx >> 2); k += Tf) {
+    const int x0 = 4 * k;
+    Row8<T> pD = ld8_row(row(phi, j0 - 1), x0, mx), pC = ld8_row(row(phi, j0), x0, mx);
+    Row8<T> sD = ld8_row(row(psi, j0 - 1), x0, mx), sC = ld8_row(row(psi, j0), x0, mx);
+    Row8<T> oD, oC;
+    if (OMEGA) {
+      oD = ld8_row(row(om, j0 - 1), x0, mx);
+      oC = ld8_row(row(om, j0), x0, mx);
+    }
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+      const int j = j0 + o;
+      const Row8<T> pU = ld8_row(row(phi, j + 1), x0, mx), sU = ld8_row(row(psi, j + 1), x0, mx);
+      Row8<T> oU;
+      if (OMEGA) oU = ld8_row(row(om, j + 1), x0, mx);
+      T dxp[4], dyp[4];
+      grad4<NEG>(sU, sC, sD, sc.w0, sc.w1, inv2h, dxp, dyp);
+      {
+        T dxf[4], dyf[4];
+        grad4<NEG>(pU, pC, pD, sc.w0, sc.w1, inv2h, dxf, dyf);
+        T r[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) r[p] = pC.v[p + 2] - dt * (dyp[p] * dxf[p] - dxp[p] * dyf[p]);
+        st4(bufp + o * nx + x0, r[0], r[1], r[2], r[3]);
+        if (gphi) st4(gphi + ((size_t)j << log2nx) + x0, r[0], r[1], r[2], r[3]);
+      }
+      if (OMEGA) {
+        T dxf[4], dyf[4];
+        grad4<NEG>(oU, oC, oD, sc.w0, sc.w1, inv2h, dxf, dyf);
+        T r[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+          r[p] = INCR ? advect_incr(dt, dyp[p], dxf[p], dxp[p], dyf[p])
+                      : oC.v[p + 2] - dt * (dyp[p] * dxf[p] - dxp[p] * dyf[p]);
+        T* brow = bufw + o * nx;
+        const int sh = o ? sh1 : sh0;
+        if (sh == 0) {
+          st4(brow + x0, r[0], r[1], r[2], r[3]);
+          if (gom) st4(gom + ((size_t)j << log2nx) + x0, r[0], r[1], r[2], r[3]);
+        } else {
+#pragma unroll
+          for (int p = 0; p < 4; ++p) {
+            brow[(x0 + p + sh) & mx] = r[p];
+            if (gom) gom[((size_t)j << log2nx) + ((x0 + p + sh) & mx)] = r[p];
+          }
+        }
+        oD = oC;
+        oC = oU;
+      }
+      pD = pC;
+      pC = pU;
+      sD = sC;
+      sC = sU;
+    }
+  }
+}
+
+template <class T, int LN, int P>
+__global__ void __launch_bounds__(rowfwd_cta_threads(P), rowfwd_min_ctas<T>(P))
+    k_stage1_rows(const MemberDesc* __restrict__ descs, int log2ny, const cplx<T>* __restrict__ tw) {
+  constexpr int log2nx = LN;
+  using C = cplx<T>;
+  constexpr int LC = Layout<T>::LC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const MemberDesc& D = descs[blockIdx.y];
+  const int nx = 1 << log2nx, ny = 1 << log2ny, my = ny - 1;
+  const int Tf = nx / P;
+  const int ipc = blockDim.x / Tf;
+  const int inst = threadIdx.x / Tf, t = threadIdx.x - inst * Tf;
+  const int nitems = ny >> 1;
+  const int stride = gridDim.x * ipc;
+  // two padded buffers per instance: phi*'s pair, then omega*'s (or a's)
+  const size_t one = stage1_inst_bytes(nx, sizeof(T));
+  T* bufp = reinterpret_cast<T*>(smem_raw + (size_t)inst * 2 * one);
+  T* bufw = reinterpret_cast<T*>(smem_raw + (size_t)inst * 2 * one + one);
+  C* tws = reinterpret_cast<C*>(smem_raw + (size_t)ipc * 2 * one);
+  stage_tables_to_smem(tws, tw, log2nx, log2_points<P>(), threadIdx.x, blockDim.x);
+  const T* phi = static_cast<const T*>(D.phi);
+  const T* psi = static_cast<const T*>(D.psi);
+  const T* om = static_cast<const T*>(D.omega);
+  const Shear<T> sc(*D.st, false);                     // s^n
+  const T dt = (T)D.dt, inv2h = (T)D.inv_2h;
+  const bool inertial = !D.stokes;
+  const bool wrap = D.remap && sc.dK != 0;
+
+  // ask L2 for item w's input rows (j0 - 1 .. j1 + 1 of phi, psi, omega)
+  auto prefetch = [&](int w) {
+    if (w < nitems && t < 4) {
+      const int j = (2 * w - 1 + t) & my;
+      const unsigned bytes = (unsigned)nx * sizeof(T);
+      l2_prefetch(phi + ((size_t)j << log2nx), bytes);
+      l2_prefetch(psi + ((size_t)j << log2nx), bytes);
+      if (inertial) l2_prefetch(om + ((size_t)j << log2nx), bytes);
+    }
+  };
+  // the row pair staged in buf (complete: the caller synchronised) -> FFT ->
+  // both half spectra into dst (and the pair's Nyquist coefficients into nyq,
+  // when not null); buf is the exchange buffer; ends with a barrier
+  auto transform_pair = [&](T* buf, bool active, C* dst, T* nyq, int p) {
+    C v[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const int i = t + q * Tf;
+      v[q] = C{buf[i], buf[nx + i]};
+    }
+    __syncthreads();                                   // buf becomes the exchange buffer
+    C* Z = reinterpret_cast<C*>(buf);
+    fft_reg<false>(v, log2nx, t, Z, tws);
+    reg_to_smem(v, log2nx, t, Z);
+    if (active) {
+      write_pair_rows<LC>(Z, dst, 2 * p, nx, ny, t, Tf);
+      if (nyq && t == 0) {
+        const C zn = Z[pad16(nx >> 1)];
+        nyq[2 * p] = zn.x;
+        nyq[2 * p + 1] = zn.y;
+      }
+    }
+    __syncthreads();                                   // Z read before buf is written again
+  };
+
+  const int iters = persistent_iters(nitems, ipc);
+  int w = blockIdx.x * ipc + inst;
+  prefetch(w);
+  for (int it = 0; it < iters; ++it, w += stride) {
+    const bool active = w < nitems;
+    const int p = active ? w : 0, j0 = 2 * p;
+    // phi* (not relabelled: phi's wrap is applied to phi^{n+1}) and omega* or a
+    T* gphi = active ? static_cast<T*>(D.phi_star) : (T*)nullptr;
+    if (inertial) {
+      const int sh0 = wrap ? remap_shift(sc.dK, D.ratio, j0, nx) : 0;
+      const int sh1 = wrap ? remap_shift(sc.dK, D.ratio, j0 + 1, nx) : 0;
+      T* gom = (active && !D.wspec) ? static_cast<T*>(D.omega_star) : (T*)nullptr;
+      if (D.wspec) {
+        if (sc.d > 0) stage1_pair<true, true, true>(phi, psi, om, bufp, bufw, gphi, gom, j0, log2nx, my, sc, dt, inv2h, t, Tf, sh0, sh1);
+        else stage1_pair<false, true, true>(phi, psi, om, bufp, bufw, gphi, gom, j0, log2nx, my, sc, dt, inv2h, t, Tf, sh0, sh1);
+      } else {
+        if (sc.d > 0) stage1_pair<true, false, true>(phi, psi, om, bufp, bufw, gphi, gom, j0, log2nx, my, sc, dt, inv2h, t, Tf, sh0, sh1);
+        else stage1_pair<false, false, true>(phi, psi, om, bufp, bufw, gphi, gom, j0, log2nx, my, sc, dt, inv2h, t, Tf, sh0, sh1);
+      }
+    } else {
+      if (sc.d > 0) stage1_pair<true, false, false>(phi, psi, om, bufp, bufw, gphi, (T*)nullptr, j0, log2nx, my, sc, dt, inv2h, t, Tf, 0, 0);
+      else stage1_pair<false, false, false>(phi, psi, om, bufp, bufw, gphi, (T*)nullptr, j0, log2nx, my, sc, dt, inv2h, t, Tf, 0, 0);
+    }
+    __syncthreads();                                   // both staged pairs complete
+    prefetch(w + stride);                              // the next item's rows, during the transforms
+    transform_pair(bufp, active, static_cast<C*>(D.xs_phi), static_cast<T*>(D.nyq_phi), p);
+    // f = phi^3 of the pre-advection pair, in the FFT's register layout (the rows are in L1/L2)
+    {
+      C v[P];
+      const T* ra = phi + ((size_t)j0 << log2nx);
+      const T* rb = ra + nx;
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        const int i = t + q * Tf;
+        const T a = ra[i], b = rb[i];
+        v[q] = C{(a * a) * a, (b * b) * b};
+      }
+      C* Z = reinterpret_cast<C*>(bufp);
+      fft_reg<false>(v, log2nx, t, Z, tws);
+      reg_to_smem(v, log2nx, t, Z);
+      if (active) write_pair_rows<LC>(Z, static_cast<C*>(D.xs_f), j0, nx, ny, t, Tf);
+      __syncthreads();
+    }
+    if (inertial)
+      transform_pair(bufw, active, static_cast<C*>(D.xs_w), D.wspec ? (T*)nullptr : static_cast<T*>(D.nyq_omega), p);
+  }
 }
 
 // one 16-byte shared-memory word as complex values (two floats pairs, or one double pair)
@@ -387,15 +555,13 @@ __global__ void __launch_bounds__(rowfwd_cta_threads(P), P == 16 ? 2 : min_ctas<
 // ----------------------------------------------------------------- launchers
 // the row kernels by variant P (points per thread; FP64 has P = 8 only) and
 // mode (0: phi, 1: g or flow), each compiled separately
+// the forward row kernels by P and mode (1: g, 2: omega into xs_w)
 template <class T, int LN>
 const void* rowfwd_fn(int P, int mode) {
   if constexpr (sizeof(T) == 4) {
-    if (P == 16)
-      return mode == 0 ? (const void*)k_rowfwd<T, LN, 16, 0>
-                       : (mode == 1 ? (const void*)k_rowfwd<T, LN, 16, 1> : (const void*)k_rowfwd<T, LN, 16, 2>);
+    if (P == 16) return mode == 1 ? (const void*)k_rowfwd<T, LN, 16, 1> : (const void*)k_rowfwd<T, LN, 16, 2>;
   }
-  return mode == 0 ? (const void*)k_rowfwd<T, LN, 8, 0>
-                   : (mode == 1 ? (const void*)k_rowfwd<T, LN, 8, 1> : (const void*)k_rowfwd<T, LN, 8, 2>);
+  return mode == 1 ? (const void*)k_rowfwd<T, LN, 8, 1> : (const void*)k_rowfwd<T, LN, 8, 2>;
 }
 template <class T, int LN>
 const void* rowinv_fn(int P, int mode) {
@@ -405,12 +571,31 @@ const void* rowinv_fn(int P, int mode) {
   return mode == 0 ? (const void*)k_rowinv<T, LN, 8, 0> : (const void*)k_rowinv<T, LN, 8, 1>;
 }
 
+template <class T, int LN>
+const void* stage1_fn(int P) {
+  if constexpr (sizeof(T) == 4) {
+    if (P == 16) return (const void*)k_stage1_rows<T, LN, 16>;
+  }
+  return (const void*)k_stage1_rows<T, LN, 8>;
+}
+
 template <class T>
 void launch_row_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int log2ny, const cplx<T>* tw,
                        const LaunchCfg& c, cudaStream_t st) {
+  if (kind == KIND_STAGE1) {
+    const dim3 grid(c.grid_x, nmem);
+    with_log2n(log2nx, [&](auto L) {
+      constexpr int LN = decltype(L)::value;
+      const MemberDesc* dd = d;
+      const cplx<T>* tt = tw;
+      void* args[] = {(void*)&dd, (void*)&log2ny, (void*)&tt};
+      cudaLaunchKernel(stage1_fn<T, LN>(c.variant), grid, dim3(c.threads), args, c.smem, st);
+    });
+    return;
+  }
   const dim3 grid(c.grid_x, nmem);
-  const bool fwd = kind == KIND_ROWFWD_PHI || kind == KIND_ROWFWD_G || kind == KIND_ROWFWD_OMEGA;
-  const int mode = (kind == KIND_ROWFWD_PHI || kind == KIND_ROWINV_PHI) ? 0 : (kind == KIND_ROWFWD_OMEGA ? 2 : 1);
+  const bool fwd = kind == KIND_ROWFWD_G || kind == KIND_ROWFWD_OMEGA;
+  const int mode = fwd ? (kind == KIND_ROWFWD_OMEGA ? 2 : 1) : (kind == KIND_ROWINV_PHI ? 0 : 1);
   with_log2n(log2nx, [&](auto L) {
     constexpr int LN = decltype(L)::value;
     const void* f = fwd ? rowfwd_fn<T, LN>(c.variant, mode) : rowinv_fn<T, LN>(c.variant, mode);
@@ -424,8 +609,16 @@ void launch_row_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int 
 template <class T>
 int row_kernel_occupancy(int kind, int log2nx, int variant, int threads, size_t smem) {
   int nb = 0;
-  const bool fwd = kind == KIND_ROWFWD_PHI || kind == KIND_ROWFWD_G;
-  const int mode = (kind == KIND_ROWFWD_PHI || kind == KIND_ROWINV_PHI) ? 0 : 1;
+  if (kind == KIND_STAGE1) {
+    with_log2n(log2nx, [&](auto L) {
+      constexpr int LN = decltype(L)::value;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, stage1_fn<T, LN>(variant), threads, smem) != cudaSuccess)
+        nb = 1;
+    });
+    return nb < 1 ? 1 : nb;
+  }
+  const bool fwd = kind == KIND_ROWFWD_G;
+  const int mode = fwd ? 1 : (kind == KIND_ROWINV_PHI ? 0 : 1);
   with_log2n(log2nx, [&](auto L) {
     constexpr int LN = decltype(L)::value;
     const void* f = fwd ? rowfwd_fn<T, LN>(variant, mode) : rowinv_fn<T, LN>(variant, mode);
@@ -440,8 +633,11 @@ void set_row_smem_limits(int lim) {
     with_log2n(ln, [&](auto L) {
       constexpr int LN = decltype(L)::value;
       for (int P : {8, 16})
+        cudaFuncSetAttribute(stage1_fn<T, LN>(P), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      for (int P : {8, 16})
         for (int mode : {0, 1, 2}) {
-          cudaFuncSetAttribute(rowfwd_fn<T, LN>(P, mode), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+          if (mode > 0)
+            cudaFuncSetAttribute(rowfwd_fn<T, LN>(P, mode), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
           if (mode < 2)
             cudaFuncSetAttribute(rowinv_fn<T, LN>(P, mode), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         }
