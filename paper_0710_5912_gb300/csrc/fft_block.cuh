@@ -7,7 +7,7 @@
 // their auto-sorted positions, so the output comes out in natural order with no
 // bit reversal.
 //
-// - fft_reg / fft_reg2 (the step kernels): each thread holds P = 8 (or 16)
+// - fft_reg (the step kernels): each thread holds P = 8 (or 16)
 //   complex values in registers; a stage is radix P (one butterfly per
 //   thread), or radix 8 / 4 / 2 for the last stage; stages exchange through a
 //   padded shared buffer.  Twiddles come from per-stage tables (below), copied
@@ -231,10 +231,6 @@ constexpr int kLogP = 3;
 __device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
 // elements of a padded exchange buffer for an N-point transform
 __host__ __device__ constexpr int padded_len(int N) { return N + N / 16; }
-// 16-byte elements (the paired exchange) are padded by one per 8: a quarter
-// warp's scatter at stride 8 then lands in 8 distinct 16-byte bank groups
-__device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
-__host__ __device__ constexpr int padded_len8(int N) { return N + N / 8; }
 
 // Per-stage twiddle tables.  A stage of radix R = 2^LR after sub-transforms of
 // length Ns = 2^a multiplies input r of butterfly k = j mod Ns by W_L^{k r},
@@ -319,11 +315,25 @@ __device__ __forceinline__ void dft_radix(C* v) {
 
 // One stage on the register layout.  LAST: keep the outputs in registers;
 // otherwise scatter them to buf (padded), barrier, gather the next stage's
-// inputs, barrier (so the buffer can be written again).
+// inputs, barrier (so the buffer can be written again).  The barrier is the
+// CTA's (CtaSync) or, for a transform owned by a whole-warp subset of the CTA,
+// a named barrier of that subset (NamedSync), so that several transforms in
+// one CTA need not wait for each other.
 template <int P> constexpr int log2_points() { return P == 16 ? 4 : 3; }
 
-template <bool INV, int LR, bool LAST, int P, class C>
-__device__ __forceinline__ void fft_reg_stage(C (&v)[P], int log2N, int log2Ns, int t, C* buf, const C* twt) {
+struct CtaSync {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct NamedSync {
+  int id, nthreads;                                    // barrier 1..15, a multiple of 32 threads
+  __device__ __forceinline__ void operator()() const {
+    asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(nthreads) : "memory");
+  }
+};
+
+template <bool INV, int LR, bool LAST, int P, class C, class Sync = CtaSync>
+__device__ __forceinline__ void fft_reg_stage(C (&v)[P], int log2N, int log2Ns, int t, C* buf, const C* twt,
+                                              const Sync& sync = Sync{}) {
   constexpr int R = 1 << LR;
   constexpr int B = P >> LR;
   const int T = 1 << (log2N - log2_points<P>());
@@ -352,10 +362,10 @@ __device__ __forceinline__ void fft_reg_stage(C (&v)[P], int log2N, int log2Ns, 
     }
   }
   if (!LAST) {
-    __syncthreads();
+    sync();
 #pragma unroll
     for (int q = 0; q < P; ++q) v[q] = buf[pad16(t + q * T)];
-    __syncthreads();
+    sync();
   }
 }
 
@@ -364,92 +374,19 @@ __device__ __forceinline__ void fft_reg_stage(C (&v)[P], int log2N, int log2Ns, 
 // the compact stage table of this length and P (compact_stage_offset) in
 // shared memory.  All threads of the CTA must call it (barriers) with the same
 // log2N.
-template <bool INV, int P, class C>
-__device__ __forceinline__ void fft_reg(C (&v)[P], int log2N, int t, C* buf, const C* tw) {
+template <bool INV, int P, class C, class Sync = CtaSync>
+__device__ __forceinline__ void fft_reg(C (&v)[P], int log2N, int t, C* buf, const C* tw, const Sync& sync = Sync{}) {
   constexpr int LP = log2_points<P>();
   int log2Ns = 0;
   while (log2N - log2Ns > LP) {
-    fft_reg_stage<INV, LP, false>(v, log2N, log2Ns, t, buf, tw);
+    fft_reg_stage<INV, LP, false>(v, log2N, log2Ns, t, buf, tw, sync);
     log2Ns += LP;
   }
   switch (log2N - log2Ns) {
-    case 4: if constexpr (P == 16) fft_reg_stage<INV, 4, true>(v, log2N, log2Ns, t, buf, tw); break;
-    case 3: fft_reg_stage<INV, 3, true>(v, log2N, log2Ns, t, buf, tw); break;
-    case 2: fft_reg_stage<INV, 2, true>(v, log2N, log2Ns, t, buf, tw); break;
-    default: fft_reg_stage<INV, 1, true>(v, log2N, log2Ns, t, buf, tw); break;
-  }
-}
-
-// Two transforms of the same length in lock step (FP32): a[] and b[] share
-// every twiddle factor, and each exchange moves both as one 16-byte vector
-// per position (buf: padded_len8(N) float4, padded by pad8).  Same register layout and stage
-// schedule as fft_reg.
-template <bool INV, int LR, bool LAST>
-__device__ __forceinline__ void fft_reg2_stage(float2 (&a)[kP], float2 (&b)[kP], int log2N, int log2Ns, int t,
-                                               float4* buf, const float2* twt) {
-  using C = float2;
-  constexpr int R = 1 << LR;
-  constexpr int B = kP >> LR;
-  const int T = 1 << (log2N - kLogP);
-  const int Ns = 1 << log2Ns;
-  C wa[R], wb[R];
-#pragma unroll
-  for (int bb = 0; bb < B; ++bb) {
-    const int j = t + bb * T;
-    const int k = j & (Ns - 1);
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      wa[r] = a[bb + r * B];
-      wb[r] = b[bb + r * B];
-    }
-    if (log2Ns > 0) {
-      C f[R];
-      load_stage_factors<R, kLogP>(twt, log2Ns, k, f);
-#pragma unroll
-      for (int r = 1; r < R; ++r) {
-        const C fr = INV ? f[r] : cconj(f[r]);
-        wa[r] = cmul(wa[r], fr);
-        wb[r] = cmul(wb[r], fr);
-      }
-    }
-    dft_radix<INV, LR>(wa);
-    dft_radix<INV, LR>(wb);
-    if (LAST) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        a[bb + r * B] = wa[r];
-        b[bb + r * B] = wb[r];
-      }
-    } else {
-      const int base = ((j - k) << LR) + k;
-#pragma unroll
-      for (int r = 0; r < R; ++r) buf[pad8(base + r * Ns)] = make_float4(wa[r].x, wa[r].y, wb[r].x, wb[r].y);
-    }
-  }
-  if (!LAST) {
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < kP; ++q) {
-      const float4 x = buf[pad8(t + q * T)];
-      a[q] = C{x.x, x.y};
-      b[q] = C{x.z, x.w};
-    }
-    __syncthreads();
-  }
-}
-
-template <bool INV>
-__device__ __forceinline__ void fft_reg2(float2 (&a)[kP], float2 (&b)[kP], int log2N, int t, float4* buf,
-                                         const float2* tw) {
-  int log2Ns = 0;
-  while (log2N - log2Ns > kLogP) {
-    fft_reg2_stage<INV, kLogP, false>(a, b, log2N, log2Ns, t, buf, tw);
-    log2Ns += kLogP;
-  }
-  switch (log2N - log2Ns) {
-    case 3: fft_reg2_stage<INV, 3, true>(a, b, log2N, log2Ns, t, buf, tw); break;
-    case 2: fft_reg2_stage<INV, 2, true>(a, b, log2N, log2Ns, t, buf, tw); break;
-    default: fft_reg2_stage<INV, 1, true>(a, b, log2N, log2Ns, t, buf, tw); break;
+    case 4: if constexpr (P == 16) fft_reg_stage<INV, 4, true>(v, log2N, log2Ns, t, buf, tw, sync); break;
+    case 3: fft_reg_stage<INV, 3, true>(v, log2N, log2Ns, t, buf, tw, sync); break;
+    case 2: fft_reg_stage<INV, 2, true>(v, log2N, log2Ns, t, buf, tw, sync); break;
+    default: fft_reg_stage<INV, 1, true>(v, log2N, log2Ns, t, buf, tw, sync); break;
   }
 }
 

@@ -180,7 +180,7 @@ LaunchCfg persistent_cfg(int kind, int nfft, int max_inst, int items, size_t ins
   LaunchCfg c{};
   const bool fwd = kind == KIND_STAGE1 || kind == KIND_ROWFWD_G;
   const bool rows = fwd || kind == KIND_ROWINV_PHI || kind == KIND_ROWINV_FLOW;
-  const int cta = rows ? rowfwd_cta_threads(P) : 512;
+  const int cta = (rows || P == 16) ? rowfwd_cta_threads(P) : 512;   // FP32 column passes: 16 points, 256 threads
   const int Tf = nfft / P;
   int log2n = 0;
   while ((1 << log2n) < nfft) ++log2n;
@@ -239,12 +239,26 @@ void configure_class_t(SizeClass& cl, Tune tune) {
                                            tune.stage1_points);
   cl.cfg[KIND_ROWFWD_G] = persistent_cfg<T>(KIND_ROWFWD_G, nx, ny / 2, ny / 2, rowfwd_inst_bytes(nx, R), nmem,
                                              tune.rowfwd_g_points);
-  // column items: whole 16-byte chunks (two modes in FP32, one in FP64)
-  const int ncol_items = R == 4 ? nx / 4 : nx / 2;
-  cl.cfg[KIND_COLPASS_PHI] =
-      persistent_cfg<T>(KIND_COLPASS_PHI, ny, ncol_items, ncol_items, colpass_inst_bytes(ny, R), nmem);
-  cl.cfg[KIND_COLPASS_FLOW] =
-      persistent_cfg<T>(KIND_COLPASS_FLOW, ny, ncol_items, ncol_items, colpass_inst_bytes(ny, R), nmem);
+  // column items: single mode columns with 16 points per thread (FP32), or
+  // whole 16-byte chunks of one complex double with 8 (FP64)
+  const int ncol_items = nx / 2;
+  const size_t colb = R == 4 ? colsingle_inst_bytes(ny) : colpass_inst_bytes(ny, R);
+  const int colP = R == 4 ? 16 : kP;
+  cl.cfg[KIND_COLPASS_PHI] = persistent_cfg<T>(KIND_COLPASS_PHI, ny, ncol_items, ncol_items, colb, nmem, colP);
+  if (R == 4 && ny >= 512) {
+    // long FP32 columns: the chunk kernel, one two-mode chunk per CTA and item
+    LaunchCfg c{};
+    c.inst_per_cta = 1;
+    c.threads = 2 * (ny / 16);
+    c.smem = colchunk_cta_bytes(ny) + stage_table_bytes(cl.log2ny, 4, R);
+    const int resident = step_kernel_occupancy<T>(KIND_COLPASS_PHI, cl.log2ny, 0, c.threads, c.smem) * sm_count();
+    int g = (resident + nmem - 1) / nmem;
+    if (g > nx / 4) g = nx / 4;
+    c.grid_x = g < 1 ? 1 : g;
+    c.grid_y = 1;
+    cl.cfg[KIND_COLPASS_PHI] = c;
+  }
+  cl.cfg[KIND_COLPASS_FLOW] = cl.cfg[KIND_COLPASS_PHI];
   const int PI = rowinv_default_points<T>();
   cl.cfg[KIND_ROWINV_PHI] = persistent_cfg<T>(KIND_ROWINV_PHI, nx, ny / 2, ny / 2, rowinv_inst_bytes(nx, R), nmem, PI);
   cl.cfg[KIND_ROWINV_FLOW] = persistent_cfg<T>(KIND_ROWINV_FLOW, nx, ny / 2, ny, rowinv_inst_bytes(nx, R), nmem, PI);

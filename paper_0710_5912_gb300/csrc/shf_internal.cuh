@@ -100,12 +100,20 @@ __host__ __device__ constexpr size_t stencil2_smem_bytes(int TX, int TY, size_t 
 __host__ __device__ constexpr size_t rowfwd_inst_bytes(int nx, size_t real_bytes) {
   return round128(2 * (size_t)nx * real_bytes + (size_t)padded_len(nx) * 2 * real_bytes);
 }
-// colpass stages two 16-byte-per-row columns (one x-spectral chunk of each
-// input field: 2 complex floats or 1 complex double per row) plus a 16-byte
-// exchange buffer (sized for the pad8 layout of the paired FP32 exchange), in
-// both precisions
+// the FP64 column pass stages two columns of 16-byte complex doubles plus
+// the padded exchange buffer
 __host__ __device__ constexpr size_t colpass_inst_bytes(int ny, size_t /*real_bytes*/) {
-  return round128((2 * (size_t)ny + (size_t)padded_len8(ny)) * 16);
+  return round128((2 * (size_t)ny + (size_t)padded_len(ny)) * 16);
+}
+// the FP32 single-mode column pass: two staged columns and the padded
+// exchange buffer, 8-byte complex elements
+__host__ __device__ constexpr size_t colsingle_inst_bytes(int ny) {
+  return round128((2 * (size_t)ny + (size_t)padded_len(ny)) * 8);
+}
+// the FP32 chunk column pass (ny >= 512): one CTA stages a two-mode chunk of
+// two fields (16-byte rows) and holds one padded exchange buffer per mode
+__host__ __device__ constexpr size_t colchunk_cta_bytes(int ny) {
+  return round128(2 * (size_t)ny * 16 + 2 * (size_t)padded_len(ny) * 8);
 }
 // the fused stage-1 row pass: per instance two padded buffers (phi*'s pair
 // and omega*'s), each holding a row pair's stencil outputs (2 nx reals) and

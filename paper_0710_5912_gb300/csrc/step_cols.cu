@@ -1,6 +1,10 @@
-// Column (y) passes of a step: k_colpass_pair (FP32, two-mode chunks) and
-// k_colpass (FP64, one mode per chunk), compiled per column length ny = 2^LN.
-// See step_kernels.cu for the step's kernels and the x-spectral layout.
+// Column (y) passes of a step, compiled per column length ny = 2^LN: in FP32
+// k_colpass_chunk (ny >= 512: a two-mode chunk per CTA, one 16-point
+// instance per mode) and k_colpass_single (shorter columns: one mode per
+// instance), both with radix-16 stages; in FP64 k_colpass (one mode per
+// 16-byte chunk, 8 points per thread).  The force's low modes (k_lowmode_cols)
+// are here too.  See step_kernels.cu for the step's kernels and the
+// x-spectral layout.
 #include "step_common.cuh"
 
 namespace shf {
@@ -215,139 +219,6 @@ __global__ void __launch_bounds__(512, min_ctas<T>()) k_colpass(const MemberDesc
   cp_async_wait_all();
 }
 
-// The FP32 column pass body for one compile-time kind (0: phi; 1: inertial
-// flow with w_hat; 2: Stokes flow; 4: the forward column transform of omega's
-// row transform into w_hat), so no per-point branch on the mode or the
-// member's regime.
-template <int LN, int KIND>
-__device__ __forceinline__ void colpass_pair_body(const MemberDesc& D, int log2nx, const float2* __restrict__ tw,
-                                                  unsigned char* smem_raw) {
-  constexpr int log2ny = LN;
-  constexpr bool two = KIND == 0 || KIND == 1;          // second input field
-  using T = float;
-  using C = float2;
-  const int nx = 1 << log2nx, ny = 1 << log2ny;
-  const int Tc = ny >> kLogP;
-  const int ipc = blockDim.x / Tc;
-  const int inst = threadIdx.x / Tc, t = threadIdx.x - inst * Tc;
-  const int nitems = KIND == 4 && !D.wspec ? 0 : nx >> 2;
-  const int stride = gridDim.x * ipc;
-  unsigned char* base = smem_raw + (size_t)inst * colpass_inst_bytes(ny, sizeof(T));
-  float4* st0 = reinterpret_cast<float4*>(base);
-  float4* st1 = st0 + ny;
-  float4* buf = st1 + ny;
-  float4* in0 = static_cast<float4*>(KIND == 0 ? D.xs_phi : (KIND == 4 ? D.xs_w : D.xs_g));
-  float4* in1 = static_cast<float4*>(KIND == 0 ? D.xs_f : D.xs_w);
-  float4* what = static_cast<float4*>(D.w_hat);
-  // a wrap during the step relabels omega_hat^n: (m, n) <- (m, n + m dK)
-  const int dK = (KIND == 1 && D.remap) ? (int)(D.st->dK & (ny - 1)) : 0;
-  float2* tws = reinterpret_cast<float2*>(smem_raw + (size_t)ipc * colpass_inst_bytes(ny, sizeof(T)));
-  stage_tables_to_smem(tws, tw, log2ny, kLogP, threadIdx.x, blockDim.x);
-
-  auto issue = [&](int cb) {
-    if (cb < nitems) {
-      copy_async(st0, in0 + (size_t)cb * ny, ny * 16, t, Tc);
-      if (two) copy_async(st1, in1 + (size_t)cb * ny, ny * 16, t, Tc);
-    }
-    cp_async_commit();
-  };
-
-  const ColConsts<T> K(D, KIND == 0 ? 0 : 1, ny);
-  const int iters = persistent_iters(nitems, ipc);
-  int cb = blockIdx.x * ipc + inst;
-  issue(cb);
-  for (int it = 0; it < iters; ++it, cb += stride) {
-    const bool active = cb < nitems;
-    cp_async_wait_all();
-    __syncthreads();
-    C a0[kP], b0[kP], a1[kP], b1[kP];                   // a: mode 2cb, b: mode 2cb+1; 0/1: the two fields
-#pragma unroll
-    for (int q = 0; q < kP; ++q) {
-      const float4 x = st0[t + q * Tc];
-      a0[q] = C{x.x, x.y};
-      b0[q] = C{x.z, x.w};
-    }
-    if (two) {
-#pragma unroll
-      for (int q = 0; q < kP; ++q) {
-        const float4 x = st1[t + q * Tc];
-        a1[q] = C{x.x, x.y};
-        b1[q] = C{x.z, x.w};
-      }
-    }
-    __syncthreads();                                    // stage free
-    issue(cb + stride);
-    fft_reg2<false>(a0, b0, log2ny, t, buf, tws);
-    if (two) fft_reg2<false>(a1, b1, log2ny, t, buf, tws);
-    const int m0 = active ? 2 * cb : 0, m1 = m0 + 1;
-    if (KIND == 4) {                                    // omega's 2D transform: the new w_hat
-      if (active) {
-        float4* o = what + (size_t)cb * ny;
-#pragma unroll
-        for (int q = 0; q < kP; ++q) o[t + q * Tc] = make_float4(a0[q].x, a0[q].y, b0[q].x, b0[q].y);
-      }
-      continue;
-    }
-    if ((KIND == 1 || KIND == 2) && D.low && m0 <= D.lowm) {   // the force's low modes
-#pragma unroll
-      for (int q = 0; q < kP; ++q) {
-        low_override(D, m0, t + q * Tc, ny, a0[q]);
-        low_override(D, m1, t + q * Tc, ny, b0[q]);
-      }
-    }
-    const double qa_d = m0 * K.qx_unit, qb_d = m1 * K.qx_unit;
-    const T qa = (T)qa_d, qb = (T)qb_d;
-    const T sqa = (T)(K.s_d * qa_d), sqb = (T)(K.s_d * qb_d);   // s q_x formed in double
-    if (KIND == 1) {
-      float4* wc = what + (size_t)(active ? cb : 0) * ny;
-      if (dK) {                                         // stage omega_hat^n so that rows can be relabelled
-#pragma unroll
-        for (int q = 0; q < kP; ++q) buf[pad8(t + q * Tc)] = wc[t + q * Tc];
-        __syncthreads();
-      }
-#pragma unroll
-      for (int q = 0; q < kP; ++q) {
-        const int nn = t + q * Tc;
-        float2 Wa, Wb;
-        if (dK) {
-          const float4 xa = buf[pad8((nn + m0 * dK) & (ny - 1))], xb = buf[pad8((nn + m1 * dK) & (ny - 1))];
-          Wa = float2{xa.x, xa.y};
-          Wb = float2{xb.z, xb.w};
-        } else {
-          const float4 x = wc[nn];
-          Wa = float2{x.x, x.y};
-          Wb = float2{x.z, x.w};
-        }
-        const float2 Na = col_multiply_wspec(K, m0, qa, sqa, nn, a0[q], a1[q], Wa);
-        const float2 Nb = col_multiply_wspec(K, m1, qb, sqb, nn, b0[q], b1[q], Wb);
-        if (active) wc[nn] = make_float4(Na.x, Na.y, Nb.x, Nb.y);
-      }
-      if (dK) __syncthreads();                          // buf is the exchange buffer again
-    } else {
-#pragma unroll
-      for (int q = 0; q < kP; ++q) {
-        col_multiply_k<KIND>(K, m0, qa, sqa, t + q * Tc, a0[q], a1[q]);
-        col_multiply_k<KIND>(K, m1, qb, sqb, t + q * Tc, b0[q], b1[q]);
-      }
-    }
-    fft_reg2<true>(a0, b0, log2ny, t, buf, tws);
-    if (active) {
-      float4* o = in0 + (size_t)cb * ny;
-#pragma unroll
-      for (int q = 0; q < kP; ++q) o[t + q * Tc] = make_float4(a0[q].x, a0[q].y, b0[q].x, b0[q].y);
-    }
-    if (KIND == 1) {
-      fft_reg2<true>(a1, b1, log2ny, t, buf, tws);
-      if (active) {
-        float4* o = in1 + (size_t)cb * ny;
-#pragma unroll
-        for (int q = 0; q < kP; ++q) o[t + q * Tc] = make_float4(a1[q].x, a1[q].y, b1[q].x, b1[q].y);
-      }
-    }
-  }
-  cp_async_wait_all();
-}
-
 // Error-free transformations in FP32 (Knuth's TwoSum; the product's error by
 // one fused multiply-add) for the double-float sums of k_lowmode_cols.
 __device__ __forceinline__ void ff_add(float& hi, float& lo, float ph, float pl) {
@@ -453,32 +324,278 @@ void launch_lowmode_cols(const MemberDesc* d, int nmem, int log2ny, const float4
   k_lowmode_cols<<<dim3((outs + 1) / 2, nmem), 256, 0, st>>>(d, log2ny, twff);
 }
 
-// FP32 column pass over whole chunks: item cb = the two modes m = 2cb, 2cb+1,
-// whose ny rows are one contiguous 16-byte-per-row run in the x-spectral
-// layout.  Both columns are staged with 16-byte copies, transformed in lock
-// step (shared twiddles, 16-byte exchanges) and written back as whole 16-byte
-// rows, so no sector is touched twice.  The kind is uniform per CTA (one
-// member per blockIdx.y).
-// KIND 0-2 as colpass_pair_body; KIND 3: flow for a launch whose members mix
-// both regimes (the body is chosen per CTA).  One kernel per kind, so each
-// gets its own register allocation.
+// The FP32 column pass on single mode columns (ny < 512): item m = one mode,
+// its ny rows staged with 8-byte copies from the two-mode chunk layout,
+// transformed with 16 points per thread (radix-16 stages), multiplied,
+// transformed back and stored 8 bytes per row.  Several instances share a
+// CTA.  Kinds: 0: phi; 1: inertial flow with w_hat; 2: Stokes flow; 4:
+// omega's forward column transform into w_hat (3: mixed, chosen per CTA).
 template <int LN, int KIND>
-__global__ void __launch_bounds__(512, 1) k_colpass_pair(const MemberDesc* __restrict__ descs, int log2nx,
-                                                        const float2* __restrict__ tw) {
+__device__ __forceinline__ void colpass_single_body(const MemberDesc& D, int log2nx, const float2* __restrict__ tw,
+                                                    unsigned char* smem_raw) {
+  constexpr int log2ny = LN;
+  constexpr int P = 16;
+  constexpr bool two = KIND == 0 || KIND == 1;          // second input field
+  using T = float;
+  using C = float2;
+  const int nx = 1 << log2nx, ny = 1 << log2ny;
+  const int Tc = ny / P;
+  const int ipc = blockDim.x / Tc;
+  const int inst = threadIdx.x / Tc, t = threadIdx.x - inst * Tc;
+  const int nitems = KIND == 4 && !D.wspec ? 0 : nx >> 1;
+  const int stride = gridDim.x * ipc;
+  unsigned char* base = smem_raw + (size_t)inst * colsingle_inst_bytes(ny);
+  C* st0 = reinterpret_cast<C*>(base);
+  C* st1 = st0 + ny;
+  C* buf = st1 + ny;
+  C* in0 = static_cast<C*>(KIND == 0 ? D.xs_phi : (KIND == 4 ? D.xs_w : D.xs_g));
+  C* in1 = static_cast<C*>(KIND == 0 ? D.xs_f : D.xs_w);
+  C* what = static_cast<C*>(D.w_hat);
+  // a wrap during the step relabels omega_hat^n: (m, n) <- (m, n + m dK)
+  const int dK = (KIND == 1 && D.remap) ? (int)(D.st->dK & (ny - 1)) : 0;
+  C* tws = reinterpret_cast<C*>(smem_raw + (size_t)ipc * colsingle_inst_bytes(ny));
+  stage_tables_to_smem(tws, tw, log2ny, 4, threadIdx.x, blockDim.x);
+
+  auto issue = [&](int m) {
+    if (m < nitems) {
+      for (int n = t; n < ny; n += Tc) {
+        cp_async8(st0 + n, in0 + xs_idx(n, m, ny, 1));
+        if (two) cp_async8(st1 + n, in1 + xs_idx(n, m, ny, 1));
+      }
+    }
+    cp_async_commit();
+  };
+
+  const ColConsts<T> K(D, KIND == 0 ? 0 : 1, ny);
+  const int iters = persistent_iters(nitems, ipc);
+  int m = blockIdx.x * ipc + inst;
+  issue(m);
+  for (int it = 0; it < iters; ++it, m += stride) {
+    const bool active = m < nitems;
+    cp_async_wait_all();
+    __syncthreads();
+    C a[P], b[P];                                       // the two fields of mode m, rows t + q Tc
+#pragma unroll
+    for (int q = 0; q < P; ++q) a[q] = st0[t + q * Tc];
+    if (two) {
+#pragma unroll
+      for (int q = 0; q < P; ++q) b[q] = st1[t + q * Tc];
+    }
+    __syncthreads();                                    // stage free
+    issue(m + stride);
+    fft_reg<false>(a, log2ny, t, buf, tws);
+    if (two) fft_reg<false>(b, log2ny, t, buf, tws);
+    const int mm = active ? m : 0;
+    if (KIND == 4) {                                    // omega's 2D transform: the new w_hat
+      if (active) {
+#pragma unroll
+        for (int q = 0; q < P; ++q) what[xs_idx(t + q * Tc, mm, ny, 1)] = a[q];
+      }
+      continue;
+    }
+    if ((KIND == 1 || KIND == 2) && D.low && mm <= D.lowm) {   // the force's low modes
+#pragma unroll
+      for (int q = 0; q < P; ++q) low_override(D, mm, t + q * Tc, ny, a[q]);
+    }
+    const double q_d = mm * K.qx_unit;
+    const T qx = (T)q_d;
+    const T sqx = (T)(K.s_d * q_d);                     // s q_x formed in double
+    if (KIND == 1) {
+      if (dK) {                                         // stage omega_hat^n so that rows can be relabelled
+#pragma unroll
+        for (int q = 0; q < P; ++q) buf[pad16(t + q * Tc)] = what[xs_idx(t + q * Tc, mm, ny, 1)];
+        __syncthreads();
+      }
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        const int nn = t + q * Tc;
+        const C Wn = dK ? buf[pad16((nn + mm * dK) & (ny - 1))] : what[xs_idx(nn, mm, ny, 1)];
+        const C Nw = col_multiply_wspec(K, mm, qx, sqx, nn, a[q], b[q], Wn);
+        if (active) what[xs_idx(nn, mm, ny, 1)] = Nw;
+      }
+      if (dK) __syncthreads();                          // buf is the exchange buffer again
+    } else {
+#pragma unroll
+      for (int q = 0; q < P; ++q) col_multiply_k<KIND>(K, mm, qx, sqx, t + q * Tc, a[q], b[q]);
+    }
+    fft_reg<true>(a, log2ny, t, buf, tws);
+    if (active) {
+#pragma unroll
+      for (int q = 0; q < P; ++q) in0[xs_idx(t + q * Tc, mm, ny, 1)] = a[q];
+    }
+    if (KIND == 1) {
+      fft_reg<true>(b, log2ny, t, buf, tws);
+      if (active) {
+#pragma unroll
+        for (int q = 0; q < P; ++q) in1[xs_idx(t + q * Tc, mm, ny, 1)] = b[q];
+      }
+    }
+  }
+  cp_async_wait_all();
+}
+
+// The FP32 column pass on whole two-mode chunks for long columns (ny >= 512):
+// the CTA stages a chunk's ny 16-byte rows of each input field (whole
+// sectors), and two 16-point instances of ny/16 threads each take one mode,
+// transform, multiply and transform back on their own exchange buffers,
+// synchronising on their own named barriers (1 and 2), so neither waits for
+// the other's stages.  The results of the two modes meet in the (then idle)
+// exchange buffers and leave as whole 16-byte rows; the CTA synchronises only
+// there and at the item boundaries.  Kinds as colpass_single_body.
+template <int LN, int KIND>
+__device__ __forceinline__ void colpass_chunk_body(const MemberDesc& D, int log2nx, const float2* __restrict__ tw,
+                                                   unsigned char* smem_raw) {
+  constexpr int log2ny = LN;
+  constexpr int ny = 1 << LN;
+  constexpr int P = 16;
+  constexpr int Tc = ny / P;                            // threads of one mode's instance (>= 32)
+  constexpr bool two = KIND == 0 || KIND == 1;
+  using T = float;
+  using C = float2;
+  const int nx = 1 << log2nx;
+  const int sub = threadIdx.x / Tc, t = threadIdx.x - sub * Tc;
+  const NamedSync sync{1 + sub, Tc};
+  const int nitems = KIND == 4 && !D.wspec ? 0 : nx >> 2;
+  const int stride = gridDim.x;
+  float4* st0 = reinterpret_cast<float4*>(smem_raw);
+  float4* st1 = st0 + ny;
+  C* buf = reinterpret_cast<C*>(st1 + ny) + (size_t)sub * padded_len(ny);
+  // after the transforms the two exchange buffers together hold one chunk's
+  // ny 16-byte rows: the two modes' results meet there and leave as whole rows
+  float4* ost = reinterpret_cast<float4*>(st1 + ny);
+  C* in0 = static_cast<C*>(KIND == 0 ? D.xs_phi : (KIND == 4 ? D.xs_w : D.xs_g));
+  C* in1 = static_cast<C*>(KIND == 0 ? D.xs_f : D.xs_w);
+  C* what = static_cast<C*>(D.w_hat);
+  const int dK = (KIND == 1 && D.remap) ? (int)(D.st->dK & (ny - 1)) : 0;
+  C* tws = reinterpret_cast<C*>(smem_raw + colchunk_cta_bytes(ny));
+  stage_tables_to_smem(tws, tw, log2ny, 4, threadIdx.x, blockDim.x);
+
+  // mode sub's values v[q] (rows t + q Tc) of chunk cb -> dst as whole 16-byte rows
+  auto store_rows = [&](const C (&v)[P], C* dst, int cb, bool active) {
+    __syncthreads();                                   // both modes' transforms are done with the buffers
+#pragma unroll
+    for (int q = 0; q < P; ++q) reinterpret_cast<C*>(ost + t + q * Tc)[sub] = v[q];
+    __syncthreads();
+    if (active) {
+      float4* o = reinterpret_cast<float4*>(dst) + (size_t)cb * ny;
+      for (int n = threadIdx.x; n < ny; n += blockDim.x) o[n] = ost[n];
+    }
+    __syncthreads();                                   // ost is the exchange buffers again
+  };
+
+  auto issue = [&](int cb) {
+    if (cb < nitems) {
+      copy_async(st0, reinterpret_cast<const float4*>(in0) + (size_t)cb * ny, ny * 16, threadIdx.x, blockDim.x);
+      if (two)
+        copy_async(st1, reinterpret_cast<const float4*>(in1) + (size_t)cb * ny, ny * 16, threadIdx.x, blockDim.x);
+    }
+    cp_async_commit();
+  };
+
+  const ColConsts<T> K(D, KIND == 0 ? 0 : 1, ny);
+  const int iters = persistent_iters(nitems, 1);
+  int cb = blockIdx.x;
+  issue(cb);
+  for (int it = 0; it < iters; ++it, cb += stride) {
+    const bool active = cb < nitems;
+    cp_async_wait_all();
+    __syncthreads();
+    C a[P], b[P];                                       // mode 2 cb + sub of the two fields
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      const float4 x = st0[t + q * Tc];
+      a[q] = sub ? C{x.z, x.w} : C{x.x, x.y};
+    }
+    if (two) {
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        const float4 x = st1[t + q * Tc];
+        b[q] = sub ? C{x.z, x.w} : C{x.x, x.y};
+      }
+    }
+    __syncthreads();                                    // stage free
+    issue(cb + stride);
+    fft_reg<false>(a, log2ny, t, buf, tws, sync);
+    if (two) fft_reg<false>(b, log2ny, t, buf, tws, sync);
+    const int mm = active ? 2 * cb + sub : sub;
+    if (KIND == 4) {                                    // omega's 2D transform: the new w_hat
+      store_rows(a, what, cb, active);
+      continue;
+    }
+    if ((KIND == 1 || KIND == 2) && D.low && mm <= D.lowm) {   // the force's low modes
+#pragma unroll
+      for (int q = 0; q < P; ++q) low_override(D, mm, t + q * Tc, ny, a[q]);
+    }
+    const double q_d = mm * K.qx_unit;
+    const T qx = (T)q_d;
+    const T sqx = (T)(K.s_d * q_d);                     // s q_x formed in double
+    if (KIND == 1) {
+      if (dK) {                                         // stage omega_hat^n so that rows can be relabelled
+#pragma unroll
+        for (int q = 0; q < P; ++q) buf[pad16(t + q * Tc)] = what[xs_idx(t + q * Tc, mm, ny, 1)];
+        sync();
+      }
+      C Nw[P];
+#pragma unroll
+      for (int q = 0; q < P; ++q) {
+        const int nn = t + q * Tc;
+        const C Wn = dK ? buf[pad16((nn + mm * dK) & (ny - 1))] : what[xs_idx(nn, mm, ny, 1)];
+        Nw[q] = col_multiply_wspec(K, mm, qx, sqx, nn, a[q], b[q], Wn);
+      }
+      store_rows(Nw, what, cb, active);                 // the new omega_hat
+    } else {
+#pragma unroll
+      for (int q = 0; q < P; ++q) col_multiply_k<KIND>(K, mm, qx, sqx, t + q * Tc, a[q], b[q]);
+    }
+    fft_reg<true>(a, log2ny, t, buf, tws, sync);
+    store_rows(a, in0, cb, active);
+    if (KIND == 1) {
+      fft_reg<true>(b, log2ny, t, buf, tws, sync);
+      store_rows(b, in1, cb, active);
+    }
+  }
+  cp_async_wait_all();
+}
+constexpr int colchunk_threads(int ln) { return 2 * ((1 << ln) / 16); }
+template <int LN, int KIND>
+__global__ void __launch_bounds__(colchunk_threads(LN), 1) k_colpass_chunk(const MemberDesc* __restrict__ descs,
+                                                                           int log2nx, const float2* __restrict__ tw) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const MemberDesc& D = descs[blockIdx.y];
-  if (KIND != 3) colpass_pair_body<LN, KIND>(D, log2nx, tw, smem_raw);
-  else if (D.stokes) colpass_pair_body<LN, 2>(D, log2nx, tw, smem_raw);
-  else colpass_pair_body<LN, 1>(D, log2nx, tw, smem_raw);
+  if (KIND != 3) colpass_chunk_body<LN, KIND>(D, log2nx, tw, smem_raw);
+  else if (D.stokes) colpass_chunk_body<LN, 2>(D, log2nx, tw, smem_raw);
+  else colpass_chunk_body<LN, 1>(D, log2nx, tw, smem_raw);
 }
+template <int LN, int KIND>
+__global__ void __launch_bounds__(256, 2) k_colpass_single(const MemberDesc* __restrict__ descs, int log2nx,
+                                                           const float2* __restrict__ tw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const MemberDesc& D = descs[blockIdx.y];
+  if (KIND != 3) colpass_single_body<LN, KIND>(D, log2nx, tw, smem_raw);
+  else if (D.stokes) colpass_single_body<LN, 2>(D, log2nx, tw, smem_raw);
+  else colpass_single_body<LN, 1>(D, log2nx, tw, smem_raw);
+}
+
+// the FP32 column kernels of a length: the chunk kernel for ny >= 512, else
+// the single-mode kernel
 template <int LN>
-const void* colpass_pair_fn(int kind) {
-  switch (kind) {
-    case 0: return (const void*)k_colpass_pair<LN, 0>;
-    case 1: return (const void*)k_colpass_pair<LN, 1>;
-    case 2: return (const void*)k_colpass_pair<LN, 2>;
-    case 4: return (const void*)k_colpass_pair<LN, 4>;
-    default: return (const void*)k_colpass_pair<LN, 3>;
+const void* colpass_fp32_fn(int kind) {
+  if constexpr (LN >= 9) {
+    switch (kind) {
+      case 0: return (const void*)k_colpass_chunk<LN, 0>;
+      case 1: return (const void*)k_colpass_chunk<LN, 1>;
+      case 2: return (const void*)k_colpass_chunk<LN, 2>;
+      case 4: return (const void*)k_colpass_chunk<LN, 4>;
+      default: return (const void*)k_colpass_chunk<LN, 3>;
+    }
+  } else {
+    switch (kind) {
+      case 0: return (const void*)k_colpass_single<LN, 0>;
+      case 1: return (const void*)k_colpass_single<LN, 1>;
+      case 2: return (const void*)k_colpass_single<LN, 2>;
+      case 4: return (const void*)k_colpass_single<LN, 4>;
+      default: return (const void*)k_colpass_single<LN, 3>;
+    }
   }
 }
 
@@ -493,13 +610,10 @@ void launch_col_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int 
     if constexpr (sizeof(T) == 4) {
       // variant of the flow pass: 1 inertial members, 2 Stokes, 3 mixed; 4: seeding w_hat
       const int k = kind == KIND_COLPASS_WINIT ? 4 : (mode == 0 ? 0 : (c.variant >= 1 && c.variant <= 3 ? c.variant : 3));
-      switch (k) {
-        case 0: k_colpass_pair<LN, 0><<<grid, c.threads, c.smem, st>>>(d, log2nx, tw); break;
-        case 1: k_colpass_pair<LN, 1><<<grid, c.threads, c.smem, st>>>(d, log2nx, tw); break;
-        case 2: k_colpass_pair<LN, 2><<<grid, c.threads, c.smem, st>>>(d, log2nx, tw); break;
-        case 4: k_colpass_pair<LN, 4><<<grid, c.threads, c.smem, st>>>(d, log2nx, tw); break;
-        default: k_colpass_pair<LN, 3><<<grid, c.threads, c.smem, st>>>(d, log2nx, tw); break;
-      }
+      const MemberDesc* dd = d;
+      const float2* tt = tw;
+      void* args[] = {(void*)&dd, (void*)&log2nx, (void*)&tt};
+      cudaLaunchKernel(colpass_fp32_fn<LN>(k), grid, dim3(c.threads), args, c.smem, st);
     } else
       k_colpass<T, LN><<<grid, c.threads, c.smem, st>>>(d, log2nx, tw, mode);
   });
@@ -511,7 +625,7 @@ int col_kernel_occupancy(int log2ny, int threads, size_t smem) {
   with_log2n(log2ny, [&](auto L) {
     constexpr int LN = decltype(L)::value;
     const void* f;
-    if constexpr (sizeof(T) == 4) f = colpass_pair_fn<LN>(3);
+    if constexpr (sizeof(T) == 4) f = colpass_fp32_fn<LN>(3);
     else f = (const void*)k_colpass<T, LN>;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads, smem) != cudaSuccess) nb = 1;
   });
@@ -525,7 +639,7 @@ void set_col_smem_limits(int lim) {
       constexpr int LN = decltype(L)::value;
       if constexpr (sizeof(T) == 4) {
         for (int k = 0; k < 5; ++k)
-          cudaFuncSetAttribute(colpass_pair_fn<LN>(k), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+          cudaFuncSetAttribute(colpass_fp32_fn<LN>(k), cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
       } else
         cudaFuncSetAttribute(k_colpass<T, LN>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
     });
