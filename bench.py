@@ -5,8 +5,10 @@ Workload: a 4096 x 4096 inertial run in FP32 (rho = eta = 1, a = b = kappa = M =
 dx = 1, gdot = 0.001, dt = 0.005) from the seeded +-0.01 quench, the large single
 run on which the metric (grid-point updates/s, FP32 against the same GPU's FP64
 path, and the fraction of the HBM roofline) is quoted.  A step is one full time
-step (eight kernel launches).  The state plus scratch (576 MiB) exceeds L2, so no
-flush is needed between steps.
+step: eight kernel launches (the stage-1 stencil fused with its row transforms,
+the phi column pass, phi's row inverse, the stage-2 stencil, g's row transforms,
+the low-mode column DFT, the flow column pass, the flow row inverse).  The state
+plus scratch exceeds L2 (129 MB), so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
@@ -369,8 +371,12 @@ def main():
     kernel_ms = g.profile_step(args.steps)
     e1.record(stream)
     e1.synchronize()
-    clk = clocks.stop()
     profiled_ms_per_step = e0.elapsed_time(e1) / args.steps
+    # the arithmetic ceilings, measured on this GPU inside the sampled-clock window
+    fma = {"fp32_tflops": shf.shf_fma_peak(shf.SHF_FP32, local_rank) / 1e12,
+           "fp64_tflops": shf.shf_fma_peak(shf.SHF_FP64, local_rank) / 1e12,
+           "method": "shf_fma_peak: 8 independent FMA chains per thread, 4 resident waves, CUDA events"}
+    clk = clocks.stop()
 
     # roofline of the dominant kernel
     peak, peak_src = measured_peaks()
@@ -487,8 +493,9 @@ def main():
                            "autotuned": {"stage1_points": tuned[0][0], "rowfwd_g_points": tuned[0][1],
                                          "stencil_rows": tuned[0][2]}},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e,
-                # nine step kernels per step plus the one state-seeding launch of the run
-                "gpu_launches": len(KERNEL_REALS_PER_POINT) * args.steps + 1,
+                # the step kernels, each launched once per step (omega_hat is seeded during the warm-up)
+                "gpu_launches": sum(1 for v in kernel_ms.values() if v > 0) * args.steps,
+                "fma_peaks": fma,
                 "profiled_ms_per_step": profiled_ms_per_step,
                 "kernel_times": "CUDA events around each launch on the grid's stream, second pass of the same K steps",
                 "step_algorithmic_bytes": step_bytes,

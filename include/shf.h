@@ -256,6 +256,19 @@ int shf_noise_fill(double* out, int64_t count, uint64_t seed, double amp);
  * NaN or Inf.  No grid is involved, so shf_last_error has no message for it. */
 int shf_mass_static(const void* d_field, int precision, int nx, int ny, void* cuda_stream, double* mean_phi);
 
+/* Measured fused multiply-add rate of one GPU, the arithmetic ceiling against
+ * which the transform passes are read.  Not a step of the method.
+ *   precision: SHF_FP32 or SHF_FP64 (the FMA type timed).
+ *   device: CUDA device ordinal; the caller's current device is restored.
+ *   flops_per_s: receives 2 x FMAs per second (0 on error).
+ * Runs independent FMA chains on every SM (a whole number of resident waves)
+ * on a stream of its own, growing the loop until one launch lasts at least
+ * 20 ms, and times that launch with CUDA events; it takes well under a second.
+ * Allocates a few bytes of device memory and frees them.  Returns SHF_EINVAL
+ * for a bad precision, device or NULL pointer, SHF_ENOMEM if the allocation
+ * fails, SHF_ECUDA for a CUDA failure. */
+int shf_fma_peak(int precision, int device, double* flops_per_s);
+
 #ifdef __cplusplus
 }
 #endif

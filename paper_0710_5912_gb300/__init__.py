@@ -102,6 +102,13 @@ def shf_mass_static(d_field, precision, nx, ny, stream=None):
     return m.value
 
 
+def shf_fma_peak(precision=SHF_FP32, device=0):
+    """Measured FMA rate of a GPU in FLOP/s (2 per fused multiply-add)."""
+    r = ctypes.c_double()
+    _check(lib().shf_fma_peak(int(precision), int(device), ctypes.byref(r)), what="shf_fma_peak")
+    return r.value
+
+
 def shf_create_grid(nx, ny, dx=1.0, precision=SHF_FP32, remap_mode=SHF_REMAP_SHIFT, stream=None):
     h = ctypes.c_void_p()
     _check(lib().shf_create_grid(ctypes.byref(h), int(nx), int(ny), float(dx), int(precision),

@@ -21,7 +21,7 @@ BUILD_DIR = os.path.join(PKG_DIR, "_build")
 LIB_DIR = os.path.join(PKG_DIR, "lib")
 LIB_PATH = os.path.join(LIB_DIR, "libshf.so")
 
-SOURCES = ["step_kernels.cu", "step_rows.cu", "step_cols.cu", "diag_kernels.cu", "shf_api.cu", "mass_static.cu"]
+SOURCES = ["step_kernels.cu", "step_rows.cu", "step_cols.cu", "diag_kernels.cu", "shf_api.cu", "mass_static.cu", "peaks.cu"]
 HEADERS = ["fft_block.cuh", "shf_internal.cuh", "step_common.cuh"]
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
@@ -145,6 +145,7 @@ SIGNATURES = {
     "shf_strain": (c_int, [c_int64, c_double, c_double, c_int, c_int, P_double, P_int64]),
     "shf_noise_fill": (c_int, [P_double, c_int64, c_uint64, c_double]),
     "shf_mass_static": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, P_double]),
+    "shf_fma_peak": (c_int, [c_int, c_int, P_double]),
 }
 
 

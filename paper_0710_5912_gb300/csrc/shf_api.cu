@@ -317,8 +317,9 @@ MemberDesc make_desc(const shf_grid* o, const Member& m) {
   d.low_rows = m.low_rows;
   d.low_hat = m.low_hat;
   d.wspec = fp32 && !d.stokes ? 1 : 0;
-  d.low = fp32 ? 1 : 0;
-  d.lowm = m.nx / 2 - 1 < kLowM ? m.nx / 2 - 1 : kLowM;
+  d.low = fp32 ? (m.rho > 0.0 ? 1 : 2) : 0;   // 2: Stokes, F's low row modes formed exactly
+  const int lowm_max = d.low == 2 ? kLowMExact : kLowM;
+  d.lowm = m.nx / 2 - 1 < lowm_max ? m.nx / 2 - 1 : lowm_max;
   d.lown = m.ny / 2 - 1 < kLowN ? m.ny / 2 - 1 : kLowN;
   return d;
 }
@@ -472,7 +473,7 @@ int build(shf_grid* g, const std::vector<int>& nx, const std::vector<int>& ny, c
     SHF_CUDA(g, cudaMemsetAsync(m.nyq, 0, 2 * (size_t)m.ny * R, g->stream));
     if (g->precision == SHF_FP32) {
       // w_hat: nx/2 x ny complex floats (the bytes of one real field); low modes of g
-      const size_t lr = (size_t)m.ny * (kLowM + 1) * sizeof(float2);
+      const size_t lr = lowrows_bytes(m.nx, m.ny);
       const size_t lh = (size_t)(kLowM + 1) * (2 * kLowN + 1) * sizeof(float2);
       if (cudaMalloc(&m.w_hat, bytes) != cudaSuccess || cudaMalloc(&m.low_rows, lr) != cudaSuccess ||
           cudaMalloc(&m.low_hat, lh) != cudaSuccess)
@@ -562,9 +563,13 @@ template <class T>
 void launch_kind(shf_grid* o, SizeClass& cl, int kind) {
   const cplx<T>* tw = static_cast<const cplx<T>*>(o->d_twr);
   if (kind == KIND_LOWMODE) {                           // FP32 only: the force's low 2D modes
-    if (sizeof(T) == 4)
-      launch_lowmode_cols(cl.d_desc, (int)cl.members.size(), cl.log2ny, static_cast<const float4*>(o->d_twff),
-                          o->stream);
+    if (sizeof(T) == 4) {
+      bool stokes = false;
+      for (int r : cl.members) stokes = stokes || o->members[r].rho == 0.0;
+      const float4* twff = static_cast<const float4*>(o->d_twff);
+      if (stokes) launch_lowrows_exact(cl.d_desc, (int)cl.members.size(), cl.log2nx, cl.log2ny, twff, o->stream);
+      launch_lowmode_cols(cl.d_desc, (int)cl.members.size(), cl.log2ny, twff, o->stream);
+    }
     return;
   }
   LaunchCfg c = cl.cfg[kind];

@@ -40,7 +40,8 @@ struct MemberDesc {
   // force computed apart (see step_cols.cu).  w_hat: the 2D DFT of omega
   // (unnormalised), nx/2 x ny complex in the column-chunk layout of the
   // column passes; low_rows: the row DFT coefficients m = 0..lowm of g's rows,
-  // ny complex per m (element m ny + j); low_hat: the 2D DFT of g at
+  // ny complex per m (element m ny + j), then a plane of the same shape with
+  // the low parts of double-float coefficients (low == 2); low_hat: the 2D DFT of g at
   // m = 0..lowm, n = -lown..lown, (2 lown + 1) complex per m.
   void* w_hat;
   void* low_rows;
@@ -60,7 +61,9 @@ struct MemberDesc {
   int remap;             // 1 when the SHIFT remap is active
   int ratio;             // nx / ny
   int wspec;             // 1: omega carried as w_hat (FP32 inertial); 0: increment form on omega*
-  int low;               // 1: the low modes of g_hat come from low_hat (FP32)
+  int low;               // FP32: the low modes of g_hat come from low_hat; their row
+                         // coefficients from the row pass's compensated sums (1,
+                         // inertial) or from k_lowrows_exact (2, Stokes); 0: FP64
   int lowm, lown;        // the low-mode window of this size: m <= lowm, |n| <= lown
   int pad_;
 };
@@ -73,6 +76,12 @@ struct MemberDesc {
 // per thread).
 constexpr int kLowM = 8;
 constexpr int kLowN = 16;
+// FP32 Stokes members form the force itself beyond FP32 for their low modes
+// (k_lowrows_exact), over m <= kLowMExact.  1/k^4 weights the FP32 rounding
+// of F by k^-8 in psi's error, yet a narrower window (m <= 4) leaves psi's
+// error twice as large after 200 steps: the rounding at m = 5..8 reaches the
+// lowest modes through the advection of phi
+constexpr int kLowMExact = 8;
 
 // Strain sawtooth of Section V from the integer step n (same operation order
 // as the host and the oracle; explicit rounding intrinsics keep the compiler
@@ -181,6 +190,10 @@ template <class T> void set_row_smem_limits(int lim);
 template <class T> void set_col_smem_limits(int lim);
 // the column DFT of the low row modes of g (FP32 members): low_rows -> low_hat;
 // twff: W[k] = exp(2 pi i k / NMAX) as (cos hi, cos lo, sin hi, sin lo)
+// bytes of a member's low_rows buffer (FP32)
+size_t lowrows_bytes(int nx, int ny);
+void launch_lowrows_exact(const MemberDesc* d, int nmem, int log2nx, int log2ny, const float4* twff,
+                          cudaStream_t st);
 void launch_lowmode_cols(const MemberDesc* d, int nmem, int log2ny, const float4* twff, cudaStream_t st);
 
 // ---- kernel launchers (step_kernels.cu / diag_kernels.cu) ----

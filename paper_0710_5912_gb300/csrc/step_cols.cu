@@ -238,7 +238,9 @@ __device__ __forceinline__ void ff_mul(float a, float bh, float bl, float& ph, f
 // The column DFT of the low row modes of g (FP32 members):
 //   low_hat[m][n + lown] = sum_j low_rows[m][j] exp(-2 pi i n j / ny),
 // m <= lowm, |n| <= lown.  Each term is the product of an FP32 coefficient
-// with a double-float twiddle, formed without rounding error to about 2^-48,
+// (a double-float one for the exact Stokes rows, low == 2, whose low part
+// adds one fused multiply-add) with a double-float twiddle, formed without
+// rounding error to about 2^-48,
 // and the four real sums (Re r cos, Im r sin, Im r cos, Re r sin) are
 // double-float sums (TwoSum), so the result carries essentially only the
 // rounding of the coefficients themselves.  A CTA holds two outputs; four
@@ -261,29 +263,32 @@ __global__ void __launch_bounds__(256) k_lowmode_cols(const MemberDesc* __restri
   const int rows = ny / kLowColsQuarters > 0 ? ny / kLowColsQuarters : 1;
   const int j0 = qtr * rows, j1 = min(ny, j0 + rows);
   const float2* lr = static_cast<const float2*>(D.low_rows) + ((size_t)m << log2ny);
+  // low parts of the coefficients (low == 2: exact Stokes rows), else none
+  const float2* lrl = D.low == 2 ? lr + ((size_t)(kLowM + 1) << log2ny) : nullptr;
   float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
   if (has) {
     for (int jb = j0; jb < j1; jb += 128) {
-      float2 r[4];
+      float2 r[4], rl[4];
       float4 w[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {                    // loads first: four rows in flight
         const int j = jb + u * 32 + lane;
         const bool in = j < j1;
         r[u] = in ? lr[j] : float2{0.f, 0.f};
+        rl[u] = in && lrl ? lrl[j] : float2{0.f, 0.f};
         w[u] = in ? __ldg(twff + (((step * j) & (ny - 1)) << tshift)) : float4{1.f, 0.f, 0.f, 0.f};
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         float ph, pl;
         ff_mul(r[u].x, w[u].x, w[u].y, ph, pl);        // Re r cos
-        ff_add(h[0], l[0], ph, pl);
+        ff_add(h[0], l[0], ph, __fmaf_rn(rl[u].x, w[u].x, pl));
         ff_mul(r[u].y, w[u].z, w[u].w, ph, pl);        // Im r sin
-        ff_add(h[1], l[1], ph, pl);
+        ff_add(h[1], l[1], ph, __fmaf_rn(rl[u].y, w[u].z, pl));
         ff_mul(r[u].y, w[u].x, w[u].y, ph, pl);        // Im r cos
-        ff_add(h[2], l[2], ph, pl);
+        ff_add(h[2], l[2], ph, __fmaf_rn(rl[u].y, w[u].x, pl));
         ff_mul(r[u].x, w[u].z, w[u].w, ph, pl);        // Re r sin
-        ff_add(h[3], l[3], ph, pl);
+        ff_add(h[3], l[3], ph, __fmaf_rn(rl[u].x, w[u].z, pl));
       }
     }
   }

@@ -69,6 +69,48 @@ __device__ __forceinline__ float kahan_add(float s, float x, float& c) {
   return t;
 }
 
+// ---- double-float arithmetic: a value carried as hi + lo, |lo| at most half
+// an ulp of hi (Dekker's and Knuth's error-free transformations; the product's
+// rounding error by one fused multiply-add).  About 44 significant bits.
+struct F2 {
+  float hi, lo;
+};
+__device__ __forceinline__ F2 f2_of(double v) {
+  const float h = (float)v;
+  return F2{h, (float)(v - (double)h)};
+}
+// Knuth's TwoSum: a + b = s + e exactly
+__device__ __forceinline__ F2 two_sum_f(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return F2{s, e};
+}
+// Dekker's FastTwoSum (|a| >= |b| or a = 0): renormalises a pair
+__device__ __forceinline__ F2 fast_two_sum_f(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return F2{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ F2 df_add(F2 a, F2 b) {
+  const F2 s = two_sum_f(a.hi, b.hi);
+  return fast_two_sum_f(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ F2 df_neg(F2 a) { return F2{-a.hi, -a.lo}; }
+__device__ __forceinline__ F2 df_mul(F2 a, F2 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return fast_two_sum_f(p, e);
+}
+// acc += x without renormalising (the low parts gather the rounding errors;
+// renormalise with fast_two_sum_f once the sum is complete)
+__device__ __forceinline__ void df_acc(F2& acc, F2 x) {
+  const F2 s = two_sum_f(acc.hi, x.hi);
+  acc.hi = s.hi;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(s.lo, x.lo));
+}
+
 // ---------------------------------------------------------------- stencils
 // four consecutive reals at a 16-byte-aligned address
 template <class T>

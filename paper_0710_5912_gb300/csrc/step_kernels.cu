@@ -199,7 +199,194 @@ __global__ void __launch_bounds__(256) k_stencil2(const MemberDesc* __restrict__
   else stencil2_body<false, T, TX, TY>(D, tp, tm, sc, x0, y0, log2nx);
 }
 
+// ======================================= exact low row modes of the Stokes force
+// The Stokes solve psi_hat = g_hat / (eta k^4) (Eq. equationNew) multiplies
+// the force's lowest modes by up to (L / 2 pi)^4.  There the curl F is a small
+// residue of much larger products, and the FP32 rounding of F at every point
+// (about eps |F|, spread over all modes) would outweigh it: psi's lowest modes
+// need F itself beyond FP32.  This kernel forms, for members with D.low == 2
+// (FP32 Stokes), the row DFT coefficients m = 0..lowm of
+//   g = c_force (D_x phi D_y^s mu - D_y^s phi D_x mu)
+// with F evaluated in double-float from the FP32 phi^{n+1} and an FP32 mu
+// (mu as the stage-2 stencil forms it): the differences of two FP32 values
+// are exact as pairs, the Eq. p1y weights w0 = 1 - |s|/2, w1 = |s|/2 come from
+// the FP64 strain, and every product and sum carries its rounding error.
+// The DFT terms F W^{m x} use the double-float twiddle table and are summed
+// as double-float pairs; the threads' sums are folded in a fixed order.  The
+// result, hi and lo planes of low_rows, feeds k_lowmode_cols like the
+// compensated sums of the row pass do for the other FP32 members.
+// Work: a CTA takes a tile of up to 32 rows x 64 columns.  phi (halo 2 rows,
+// 3 columns) and mu (halo 1 row, 2 columns) of the tile sit in shared memory;
+// lane r of every warp owns row j0 + r and its warp's slice of the columns,
+// so a thread sums its own row and the twiddle W^{m x} is the same for the
+// whole warp (one broadcast load).  The 8 warps' sums of a row are folded in
+// warp order; with several column tiles per row the CTAs park their sums in
+// a scratch area and the last CTA of a row block to finish (an atomic
+// counter; nothing waits) folds them in tile order into low_rows.
+constexpr int kLxRows = 32;     // rows per CTA: one per lane
+constexpr int kLxCols = 64;     // columns per CTA
+constexpr int kLxWarps = 8;
+constexpr int kLxValues = 2 * (kLowMExact + 1);   // Re and Im of m = 0..kLowMExact
+__host__ __device__ constexpr int lowexact_cols(int nx) { return nx < kLxCols ? nx : kLxCols; }
+__host__ __device__ constexpr int lowexact_rows(int ny) { return ny < kLxRows ? ny : kLxRows; }
+__host__ __device__ constexpr int lowexact_pitch_phi(int xt) { return (xt + 6) | 1; }
+__host__ __device__ constexpr int lowexact_pitch_mu(int xt) { return (xt + 4) | 1; }
+__host__ __device__ constexpr int lowexact_smem_floats(int nx, int ny) {
+  return (lowexact_rows(ny) + 4) * lowexact_pitch_phi(lowexact_cols(nx)) +
+                 (lowexact_rows(ny) + 2) * lowexact_pitch_mu(lowexact_cols(nx)) >
+                 2 * kLxValues * kLxWarps * kLxRows
+             ? (lowexact_rows(ny) + 4) * lowexact_pitch_phi(lowexact_cols(nx)) +
+                   (lowexact_rows(ny) + 2) * lowexact_pitch_mu(lowexact_cols(nx))
+             : 2 * kLxValues * kLxWarps * kLxRows;
+}
+// acc += F w for an FP32-pair F and a double-float w: the product's rounding
+// error by fused multiply-adds, the low parts added unnormalised
+__device__ __forceinline__ void df_acc_prod(F2& acc, F2 F, float wh, float wl) {
+  const float p = __fmul_rn(F.hi, wh);
+  float e = __fmaf_rn(F.hi, wh, -p);
+  e = __fmaf_rn(F.hi, wl, e);
+  e = __fmaf_rn(F.lo, wh, e);
+  const F2 s = two_sum_f(acc.hi, p);
+  acc.hi = s.hi;
+  acc.lo = __fadd_rn(acc.lo, __fadd_rn(s.lo, e));
+}
+__global__ void __launch_bounds__(kLxWarps * 32) k_lowrows_exact(const MemberDesc* __restrict__ descs, int log2nx,
+                                                                 int log2ny, const float4* __restrict__ twff) {
+  const MemberDesc& D = descs[blockIdx.z];
+  if (D.low != 2) return;                              // uniform per CTA
+  extern __shared__ __align__(16) float sm[];
+  const int nx = 1 << log2nx, ny = 1 << log2ny, mx = nx - 1, my = ny - 1;
+  const int XT = lowexact_cols(nx), RT = lowexact_rows(ny);
+  const int PP = lowexact_pitch_phi(XT), PM = lowexact_pitch_mu(XT);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int x0 = blockIdx.x * XT, j0 = blockIdx.y * RT;
+  const float* phi = static_cast<const float*>(D.phi);
+  float* tp = sm;                                      // phi rows j0 - 2 + r, cols x0 - 3 + c
+  float* tm = sm + (RT + 4) * PP;                      // mu rows j0 - 1 + r, cols x0 - 2 + c
+  for (int e = tid; e < (RT + 4) * (XT + 6); e += nt) {
+    const int r = e / (XT + 6), c = e - r * (XT + 6);
+    tp[r * PP + c] = __ldg(phi + ((size_t)((j0 - 2 + r) & my) << log2nx) + ((x0 - 3 + c) & mx));
+  }
+  __syncthreads();
+  const Shear<float> sc(*D.st, true);                  // s^{n+1}
+  {                                                    // mu in FP32, as the stage-2 stencil forms it
+    const float a = (float)D.a, b = (float)D.b, kappa = (float)D.kappa;
+    const float cxx = 1.f + sc.s * sc.s, cxy = 2.f * sc.s;
+    const float kxx = kappa * cxx * (float)D.inv_h2, kxy = kappa * cxy * (float)D.inv_4h2,
+                kyy = kappa * (float)D.inv_h2;
+    for (int e = tid; e < (RT + 2) * (XT + 4); e += nt) {
+      const int r = e / (XT + 4), c = e - r * (XT + 4);
+      const float* pc_ = tp + (r + 1) * PP + (c + 1);  // the centre in the phi tile
+      const float pc = pc_[0];
+      const float sxx = pc_[1] - 2.f * pc + pc_[-1];
+      const float syy = pc_[PP] - 2.f * pc + pc_[-PP];
+      const float sxy = pc_[PP + 1] - pc_[-PP + 1] - pc_[PP - 1] + pc_[-PP - 1];
+      const float klap = kxx * sxx - kxy * sxy + kyy * syy;
+      tm[r * PM + c] = pc * (b * (pc * pc) - a) - klap;
+    }
+  }
+  __syncthreads();
+  const double s1 = D.st->s1;
+  const double w1d = 0.5 * (s1 < 0.0 ? -s1 : s1);
+  const F2 W0 = f2_of(1.0 - w1d), W1 = f2_of(w1d);
+  const F2 KF = f2_of(D.c_force * D.inv_2h * D.inv_2h);
+  const int dd = sc.d;                                 // the diagonal's x offset at row j + 1
+  const int lowm = D.lowm, nv = 2 * (lowm + 1);
+  const int tshift = LOG2_NMAX - log2nx;
+  const int lane = tid & 31, warp = tid >> 5;
+  const int cw = XT / kLxWarps > 0 ? XT / kLxWarps : 1;        // columns per warp
+  const int c0 = warp * cw, c1 = min(XT, c0 + cw);
+  F2 acc[kLxValues];
+#pragma unroll
+  for (int k = 0; k < kLxValues; ++k) acc[k] = F2{0.f, 0.f};
+  if (lane < RT) {
+    const float* prow = tp + (lane + 2) * PP + 3;     // phi row j, col 0 of the tile
+    const float* mrow = tm + (lane + 1) * PM + 2;     // mu row j
+    for (int c = c0; c < c1; ++c) {
+      const float* p = prow + c;
+      const float* q = mrow + c;
+      const F2 dxp = two_sum_f(p[1], -p[-1]);
+      const F2 dxm = two_sum_f(q[1], -q[-1]);
+      const F2 dyp = df_add(df_mul(W0, two_sum_f(p[PP], -p[-PP])), df_mul(W1, two_sum_f(p[PP + dd], -p[-PP - dd])));
+      const F2 dym = df_add(df_mul(W0, two_sum_f(q[PM], -q[-PM])), df_mul(W1, two_sum_f(q[PM + dd], -q[-PM - dd])));
+      const F2 F = df_mul(df_add(df_mul(dxp, dym), df_neg(df_mul(dyp, dxm))), KF);
+      df_acc(acc[0], F);
+      const int x = x0 + c;
+#pragma unroll
+      for (int m = 1; m <= kLowMExact; ++m) {
+        if (m > lowm) break;
+        const float4 w = __ldg(twff + (((m * x) & mx) << tshift));   // cos, sin of 2 pi m x / nx as pairs
+        df_acc_prod(acc[2 * m], F, w.x, w.y);
+        df_acc_prod(acc[2 * m + 1], F, -w.z, -w.w);
+      }
+    }
+  }
+  __syncthreads();                                     // tiles no longer read: the fold reuses them
+  float* red = sm;                                     // value v, warp w, lane r: [(2 v) W + w] 32 + r
+#pragma unroll
+  for (int v = 0; v < kLxValues; ++v) {
+    if (v >= nv) break;
+    const F2 r = fast_two_sum_f(acc[v].hi, acc[v].lo);
+    red[((2 * v) * kLxWarps + warp) * 32 + lane] = r.hi;
+    red[((2 * v + 1) * kLxWarps + warp) * 32 + lane] = r.lo;
+  }
+  __syncthreads();
+  // item e < RT nv: row r = e mod RT, value v = e / RT, the warps in order
+  const int nxb = gridDim.x;
+  float2* lrh = static_cast<float2*>(D.low_rows);
+  float2* lrl = lrh + ((size_t)(kLowM + 1) << log2ny);
+  float2* part = lrl + ((size_t)(kLowM + 1) << log2ny);           // [tile][v][row] (hi, lo)
+  int* cnt = reinterpret_cast<int*>(part + ((size_t)nxb * kLxValues << log2ny));
+  for (int e = tid; e < RT * nv; e += nt) {
+    const int r = e % RT, v = e / RT;
+    F2 sum{0.f, 0.f};
+    for (int w = 0; w < kLxWarps; ++w)
+      sum = df_add(sum, F2{red[((2 * v) * kLxWarps + w) * 32 + r], red[((2 * v + 1) * kLxWarps + w) * 32 + r]});
+    const int j = j0 + r, m = v >> 1;
+    if (nxb == 1) {
+      reinterpret_cast<float*>(lrh + ((size_t)m << log2ny) + j)[v & 1] = sum.hi;
+      reinterpret_cast<float*>(lrl + ((size_t)m << log2ny) + j)[v & 1] = sum.lo;
+    } else {
+      part[(((size_t)blockIdx.x * kLxValues + v) << log2ny) + j] = float2{sum.hi, sum.lo};
+    }
+  }
+  if (nxb == 1) return;
+  __threadfence();                                     // this tile's sums visible before it is counted
+  __syncthreads();
+  __shared__ int last;
+  if (tid == 0) last = atomicAdd(cnt + blockIdx.y, 1) == nxb - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int e = tid; e < RT * nv; e += nt) {
+    const int r = e % RT, v = e / RT;
+    const int j = j0 + r, m = v >> 1;
+    F2 tot{0.f, 0.f};
+    for (int xb = 0; xb < nxb; ++xb) {
+      const float2 pv = __ldcg(part + (((size_t)xb * kLxValues + v) << log2ny) + j);
+      tot = df_add(tot, F2{pv.x, pv.y});
+    }
+    reinterpret_cast<float*>(lrh + ((size_t)m << log2ny) + j)[v & 1] = tot.hi;
+    reinterpret_cast<float*>(lrl + ((size_t)m << log2ny) + j)[v & 1] = tot.lo;
+  }
+  if (tid == 0) cnt[blockIdx.y] = 0;                   // ready for the next step
+}
+
 // ----------------------------------------------------------------- launchers
+void launch_lowrows_exact(const MemberDesc* d, int nmem, int log2nx, int log2ny, const float4* twff,
+                          cudaStream_t st) {
+  const int nx = 1 << log2nx, ny = 1 << log2ny;
+  const size_t smem = (size_t)lowexact_smem_floats(nx, ny) * sizeof(float);
+  const dim3 grid(nx / lowexact_cols(nx), ny / lowexact_rows(ny), nmem);
+  k_lowrows_exact<<<grid, kLxWarps * 32, smem, st>>>(d, log2nx, log2ny, twff);
+}
+size_t lowrows_bytes(int nx, int ny) {
+  // hi and lo planes of the coefficients, the exact path's per-tile sums and
+  // its row-block counters
+  return 2 * (size_t)(kLowM + 1) * ny * sizeof(float2) +
+         (size_t)(nx / lowexact_cols(nx)) * kLxValues * ny * sizeof(float2) +
+         (size_t)(ny / lowexact_rows(ny)) * sizeof(int);
+}
 void launch_step_state_init(const MemberDesc* d, int nmem, cudaStream_t st) {
   k_step_state_init<<<(nmem + 127) / 128, 128, 0, st>>>(d, nmem);
 }
@@ -264,6 +451,7 @@ void set_step_smem_limits() {
   set_col_smem_limits<T>(lim);
   stencil_smem_limits_ty<T, 16>(lim);
   stencil_smem_limits_ty<T, 32>(lim);
+  if (sizeof(T) == 4) cudaFuncSetAttribute(k_lowrows_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 
 #define SHF_INST(T)                                                                                      \

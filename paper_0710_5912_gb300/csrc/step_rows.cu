@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(rowfwd_cta_threads(P), rowfwd_min_ctas<T>(P)) 
     cp_async_wait_all();
     __syncthreads();
     if constexpr (sizeof(T) == 4 && P == 16 && MODE == 1) {   // the force's low row modes, part 1
-      if (D.low) low_row_terms<LN>(reinterpret_cast<const float*>(stage), reinterpret_cast<float*>(Z), tws, t, D);
+      if (D.low == 1) low_row_terms<LN>(reinterpret_cast<const float*>(stage), reinterpret_cast<float*>(Z), tws, t, D);
     }
     C v[P];
 #pragma unroll
@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(rowfwd_cta_threads(P), rowfwd_min_ctas<T>(P)) 
     __syncthreads();                                    // stage free
     issue(w + stride);                                  // next item streams in during the transform
     if constexpr (sizeof(T) == 4 && P == 16 && MODE == 1) {
-      if (D.low) low_row_reduce<LN>(reinterpret_cast<float*>(Z), t, D, p, active, log2ny);
+      if (D.low == 1) low_row_reduce<LN>(reinterpret_cast<float*>(Z), t, D, p, active, log2ny);
     }
     fft_reg<false>(v, log2nx, t, Z, tws);
     reg_to_smem(v, log2nx, t, Z);
