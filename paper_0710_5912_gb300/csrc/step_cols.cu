@@ -243,53 +243,51 @@ __device__ __forceinline__ void ff_mul(float a, float bh, float bl, float& ph, f
 // rounding error to about 2^-48,
 // and the four real sums (Re r cos, Im r sin, Im r cos, Re r sin) are
 // double-float sums (TwoSum), so the result carries essentially only the
-// rounding of the coefficients themselves.  A CTA holds two outputs; four
-// warps share one output's rows in quarters (lanes coalesced along j, four
-// rows in flight per lane); lanes and quarters are folded in a fixed order,
-// as float pairs.
-constexpr int kLowColsQuarters = 4;
-__global__ void __launch_bounds__(256) k_lowmode_cols(const MemberDesc* __restrict__ descs, int log2ny,
-                                                      const float4* __restrict__ twff) {
+// rounding of the coefficients themselves.  A CTA holds one output; its
+// eight warps share the rows in eighths (lanes coalesced along j, four rows in
+// flight per lane); lanes and warps are folded in a fixed order, as float
+// pairs.
+constexpr int kLowColsWarps = 8;
+__global__ void __launch_bounds__(kLowColsWarps * 32) k_lowmode_cols(const MemberDesc* __restrict__ descs,
+                                                                     int log2ny, const float4* __restrict__ twff) {
   const MemberDesc& D = descs[blockIdx.y];
   if (!D.low) return;                                  // uniform per CTA
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int o = blockIdx.x * 2 + (warp >> 2), qtr = warp & 3;
+  const int o = blockIdx.x;
   const int nn = 2 * D.lown + 1;
-  const bool has = o < (D.lowm + 1) * nn;
-  const int m = has ? o / nn : 0, ns = has ? o - m * nn - D.lown : 0;
+  if (o >= (D.lowm + 1) * nn) return;                  // uniform per CTA
+  const int m = o / nn, ns = o - m * nn - D.lown;
   const int ny = 1 << log2ny;
   const int tshift = LOG2_NMAX - log2ny;
   const int step = ns & (ny - 1);
-  const int rows = ny / kLowColsQuarters > 0 ? ny / kLowColsQuarters : 1;
-  const int j0 = qtr * rows, j1 = min(ny, j0 + rows);
+  const int rows = ny / kLowColsWarps > 0 ? ny / kLowColsWarps : 1;
+  const int j0 = warp * rows, j1 = min(ny, j0 + rows);
   const float2* lr = static_cast<const float2*>(D.low_rows) + ((size_t)m << log2ny);
   // low parts of the coefficients (low == 2: exact Stokes rows), else none
   const float2* lrl = D.low == 2 ? lr + ((size_t)(kLowM + 1) << log2ny) : nullptr;
   float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
-  if (has) {
-    for (int jb = j0; jb < j1; jb += 128) {
-      float2 r[4], rl[4];
-      float4 w[4];
+  for (int jb = j0; jb < j1; jb += 128) {
+    float2 r[4], rl[4];
+    float4 w[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {                    // loads first: four rows in flight
-        const int j = jb + u * 32 + lane;
-        const bool in = j < j1;
-        r[u] = in ? lr[j] : float2{0.f, 0.f};
-        rl[u] = in && lrl ? lrl[j] : float2{0.f, 0.f};
-        w[u] = in ? __ldg(twff + (((step * j) & (ny - 1)) << tshift)) : float4{1.f, 0.f, 0.f, 0.f};
-      }
+    for (int u = 0; u < 4; ++u) {                      // loads first: four rows in flight
+      const int j = jb + u * 32 + lane;
+      const bool in = j < j1;
+      r[u] = in ? lr[j] : float2{0.f, 0.f};
+      rl[u] = in && lrl ? lrl[j] : float2{0.f, 0.f};
+      w[u] = in ? __ldg(twff + (((step * j) & (ny - 1)) << tshift)) : float4{1.f, 0.f, 0.f, 0.f};
+    }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        float ph, pl;
-        ff_mul(r[u].x, w[u].x, w[u].y, ph, pl);        // Re r cos
-        ff_add(h[0], l[0], ph, __fmaf_rn(rl[u].x, w[u].x, pl));
-        ff_mul(r[u].y, w[u].z, w[u].w, ph, pl);        // Im r sin
-        ff_add(h[1], l[1], ph, __fmaf_rn(rl[u].y, w[u].z, pl));
-        ff_mul(r[u].y, w[u].x, w[u].y, ph, pl);        // Im r cos
-        ff_add(h[2], l[2], ph, __fmaf_rn(rl[u].y, w[u].x, pl));
-        ff_mul(r[u].x, w[u].z, w[u].w, ph, pl);        // Re r sin
-        ff_add(h[3], l[3], ph, __fmaf_rn(rl[u].x, w[u].z, pl));
-      }
+    for (int u = 0; u < 4; ++u) {
+      float ph, pl;
+      ff_mul(r[u].x, w[u].x, w[u].y, ph, pl);          // Re r cos
+      ff_add(h[0], l[0], ph, __fmaf_rn(rl[u].x, w[u].x, pl));
+      ff_mul(r[u].y, w[u].z, w[u].w, ph, pl);          // Im r sin
+      ff_add(h[1], l[1], ph, __fmaf_rn(rl[u].y, w[u].z, pl));
+      ff_mul(r[u].y, w[u].x, w[u].y, ph, pl);          // Im r cos
+      ff_add(h[2], l[2], ph, __fmaf_rn(rl[u].y, w[u].x, pl));
+      ff_mul(r[u].x, w[u].z, w[u].w, ph, pl);          // Re r sin
+      ff_add(h[3], l[3], ph, __fmaf_rn(rl[u].x, w[u].z, pl));
     }
   }
   // fold the lanes pairwise in a fixed tree, every sum kept as a float pair
@@ -300,7 +298,7 @@ __global__ void __launch_bounds__(256) k_lowmode_cols(const MemberDesc* __restri
       if (lane < off) ff_add(h[k], l[k], oh, ol);
     }
   }
-  __shared__ float part[8][8];
+  __shared__ float part[kLowColsWarps][8];
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -309,24 +307,21 @@ __global__ void __launch_bounds__(256) k_lowmode_cols(const MemberDesc* __restri
     }
   }
   __syncthreads();
-  if (threadIdx.x < 2) {                               // the four quarters in order
-    const int oo = blockIdx.x * 2 + threadIdx.x;
-    if (oo < (D.lowm + 1) * nn) {
-      float H[4] = {0.f, 0.f, 0.f, 0.f}, L[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int q = 0; q < kLowColsQuarters; ++q)
+  if (threadIdx.x == 0) {                              // the warps in order
+    float H[4] = {0.f, 0.f, 0.f, 0.f}, L[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int q = 0; q < kLowColsWarps; ++q)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) ff_add(H[k], L[k], part[4 * threadIdx.x + q][k], part[4 * threadIdx.x + q][4 + k]);
-      // r conj(w): Re = Re r cos + Im r sin, Im = Im r cos - Re r sin
-      ff_add(H[0], L[0], H[1], L[1]);
-      ff_add(H[2], L[2], -H[3], -L[3]);
-      static_cast<float2*>(D.low_hat)[oo] = float2{__fadd_rn(H[0], L[0]), __fadd_rn(H[2], L[2])};
-    }
+      for (int k = 0; k < 4; ++k) ff_add(H[k], L[k], part[q][k], part[q][4 + k]);
+    // r conj(w): Re = Re r cos + Im r sin, Im = Im r cos - Re r sin
+    ff_add(H[0], L[0], H[1], L[1]);
+    ff_add(H[2], L[2], -H[3], -L[3]);
+    static_cast<float2*>(D.low_hat)[o] = float2{__fadd_rn(H[0], L[0]), __fadd_rn(H[2], L[2])};
   }
 }
 
 void launch_lowmode_cols(const MemberDesc* d, int nmem, int log2ny, const float4* twff, cudaStream_t st) {
   const int outs = (kLowM + 1) * (2 * kLowN + 1);
-  k_lowmode_cols<<<dim3((outs + 1) / 2, nmem), 256, 0, st>>>(d, log2ny, twff);
+  k_lowmode_cols<<<dim3(outs, nmem), kLowColsWarps * 32, 0, st>>>(d, log2ny, twff);
 }
 
 // The FP32 column pass on single mode columns (ny < 512): item m = one mode,

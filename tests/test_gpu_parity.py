@@ -19,7 +19,7 @@ import pytest
 
 import oracle
 import paper_0710_5912_gb300 as shf
-from paper_0710_5912_gb300 import inputs
+from paper_0710_5912_gb300 import configs, inputs
 from fp32_model import PSI32_MODEL_MAX, psi32_model_ratio
 
 torch = pytest.importorskip("torch")
@@ -182,6 +182,35 @@ def test_paper_geometry_1024x512_across_a_wrap(prec, rho):
     got = gpu_run(nx, ny, prec, p, fields, 28, 8)
     want = oracle_run(p, fields, 28, 8)
     assert_close(got, want, TOL_200[prec], rho, f"1024x512 rho={rho}", prec, s_end, 1.0)
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+@pytest.mark.parametrize("name", ["R028s", "R030s", "DV4s", "DV6s"])
+def test_table_I_parameters_across_the_first_wrap(prec, name):
+    """Table I sets (c: sheared with inertia; d: sheared without) in the
+    paper's units (Section IV: dx = Lambda_y / 512, kappa = M = l^2,
+    Lambda_x = 2) on 1024 x 512: 8 steps across the first strain wrap, where
+    |s| reaches 1 and the remap shifts row j by 2j cells, from a rough phi
+    (+-0.05) at rest, against the oracle."""
+    nx, ny, dx, pp = configs.paper_units(name)
+    p = oracle.Params(dx=dx, **pp)
+    n_wrap = int(math.ceil(1.0 / (p.gdot * p.dt)))
+    while oracle.strain(n_wrap, p.gdot, p.dt, nx, ny)[1] == 0:
+        n_wrap += 1
+    while oracle.strain(n_wrap - 1, p.gdot, p.dt, nx, ny)[1] == 1:
+        n_wrap -= 1
+    n0 = n_wrap - 4
+    s_before = oracle.strain(n0 + 3, p.gdot, p.dt, nx, ny)[0]
+    assert s_before > 0.95                              # |s| near 1 just before the wrap
+    phi = 0.1 * inputs.quench_noise(nx, ny, 31, 0.5)
+    zero = np.zeros((ny, nx))
+    fields = (phi, zero, zero)
+    got = gpu_run(nx, ny, prec, p, fields, n0, 8)
+    want = oracle_run(p, fields, n0, 8)
+    s_end = oracle.strain(n0 + 8, p.gdot, p.dt, nx, ny)[0]
+    for nm, a, b in zip(("phi", "psi", "omega"), got, want):
+        print(f"{name} {'fp32' if prec == FP32 else 'fp64'} {nm}: rel L2 {rel_l2(a, b):.3e}")
+    assert_close(got, want, TOL_200[prec], p.rho, f"{name}", prec, s_end, dx)
 
 
 @pytest.mark.parametrize("rho", [0.0, 0.1, 1.0])
