@@ -5,9 +5,9 @@ Workload: a 4096 x 4096 inertial run in FP32 (rho = eta = 1, a = b = kappa = M =
 dx = 1, gdot = 0.001, dt = 0.005) from the seeded +-0.01 quench, the large single
 run on which the metric (grid-point updates/s, FP32 against the same GPU's FP64
 path, and the fraction of the HBM roofline) is quoted.  A step is one full time
-step: eight kernel launches (the stage-1 stencil fused with its row transforms,
-the phi column pass, phi's row inverse, the stage-2 stencil, g's row transforms,
-the low-mode column DFT, the flow column pass, the flow row inverse).  The state
+step: seven kernel launches (the stage-1 stencil fused with its row transforms,
+the phi column pass, phi's row inverse, the stage-2 stencil fused with g's row
+transform, the low-mode column DFT, the flow column pass, the flow row inverse).  The state
 plus scratch exceeds L2 (129 MB), so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
@@ -47,8 +47,7 @@ KERNEL_REALS_PER_POINT = {
     "stage1": 7,          # phi, psi, omega in; phi* (real), phi*, f, a (x-spectral) out
     "colpass_phi": 3,     # phi*, f in; phi increment out
     "rowinv_phi": 3,      # increment, phi* in; phi out
-    "stencil2": 2,        # phi in; g out
-    "rowfwd_g": 2,        # g in; g (x-spectral) out (+ 9 low coefficients per row)
+    "stage2": 2,          # phi in; g (x-spectral) out (+ 9 low coefficients per row)
     "lowmode": 0,         # 9 x 33 low modes of g from 9 coefficients per row (~0.6 B per point)
     "colpass_flow": 6,    # g, a, omega_hat in; omega_hat, psi, omega (x-spectral) out
     "rowinv_flow": 4,     # psi, omega (x-spectral) in; psi, omega out
@@ -490,8 +489,7 @@ def main():
                 "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, **PARAMS, "seed": SEED, "amp": AMP,
                            "parallelism": f"replicas x{world}" if world > 1 else "single grid",
                            "l2": "state + scratch 576 MiB > L2 (129 MB): inputs larger than L2, no flush",
-                           "autotuned": {"stage1_points": tuned[0][0], "rowfwd_g_points": tuned[0][1],
-                                         "stencil_rows": tuned[0][2]}},
+                           "autotuned": {"stage1_points": tuned[0][0], "stage2_points": tuned[0][1]}},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e,
                 # the step kernels, each launched once per step (omega_hat is seeded during the warm-up)
                 "gpu_launches": sum(1 for v in kernel_ms.values() if v > 0) * args.steps,

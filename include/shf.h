@@ -139,10 +139,11 @@ int shf_step(shf_grid* g, int64_t nsteps);
 
 /* Advance nsteps >= 1 steps like shf_step, but launch every kernel directly
  * with a CUDA event recorded on the grid's stream before and after it, and
- * return in kernel_ms[0..7] the mean device time per step of each of the eight
- * launches of a step (stage-1 stencil, phi row transforms, phi column pass,
- * phi row inverse, stage-2 stencil, g row transform, flow column pass, flow
- * row inverse), summed over size classes.  nkinds must be >= 8.
+ * return in kernel_ms[0..6] the mean device time per step of each of the seven
+ * launches of a step (stage-1 stencil with the row transforms of phi*, f,
+ * omega*; phi column pass; phi row inverse; stage-2 stencil with the row
+ * transform of g; the force's low modes (FP32 only, 0 for FP64); flow column
+ * pass; flow row inverse), summed over size classes.  nkinds must be >= 7.
  * Synchronising; meant for measurement (per-kernel roofline), not for
  * production runs. */
 int shf_profile_step(shf_grid* g, int64_t nsteps, double* kernel_ms, int nkinds);
@@ -184,16 +185,15 @@ int shf_gradient_tensor(shf_grid* g, double G[3], double lengths[2]);
 /* Pick, per size class, the launch variants that run fastest on this GPU:
  * the fused stage-1 row pass (the stage-1 stencil with the row transforms of
  * phi*, f, omega*) with 8 or 16 points per thread (radix-8 or radix-16
- * stages; FP32 only) and the stage-2 stencil tile height (16 or 32 rows).
- * The g row pass keeps 16 points in FP32 (its first stage yields the force's
- * low modes).
+ * stages; FP32 only).  The fused stage-2 row pass keeps 16 points in FP32
+ * (its first stage yields the force's low modes) and 8 in FP64.
  * Each candidate's kernels are timed on the grid's own buffers; only kernels
  * that write scratch buffers run, so the state (fields, step) is unchanged and
  * results stay within the parity tolerances (the variants round differently).
  * cache_path (nullable): a JSON file of earlier choices keyed by
  * "NXxNY:fp32|fp64:inertial|stokes|mixed"; keys found there are applied
  * without trials, new ones are added.  choices (nullable, nchoices ints):
- * receives (stage1_points, rowfwd_g_points, stencil_rows) per size class,
+ * receives (stage1_points, stage2_points) per size class,
  * in order of first appearance among the members.  Parameters must be set.  Not for member
  * views.  SHF_EIO if the cache cannot be written.  The paper has no
  * counterpart: this is a performance knob of the implementation. */

@@ -146,8 +146,7 @@ def shf_step(h, nsteps=1):
     _check(lib().shf_step(h, int(nsteps)), h, "shf_step")
 
 
-KERNEL_KINDS = ("stage1", "colpass_phi", "rowinv_phi", "stencil2", "rowfwd_g", "lowmode", "colpass_flow",
-                "rowinv_flow")
+KERNEL_KINDS = ("stage1", "colpass_phi", "rowinv_phi", "stage2", "lowmode", "colpass_flow", "rowinv_flow")
 
 
 def shf_profile_step(h, nsteps):
@@ -226,12 +225,12 @@ def shf_step_host_f32(h, nx, ny, nsteps, phi=None, psi=None, omega=None, out=Non
 
 def shf_autotune(h, cache_path=None, nclasses=8):
     """Tune the launch variants per size class; returns
-    [(stage1_points, rowfwd_g_points, stencil_rows), ...]."""
-    out = (ctypes.c_int * (3 * nclasses))()
+    [(stage1_points, stage2_points), ...]."""
+    out = (ctypes.c_int * (2 * nclasses))()
     path = None if cache_path is None else str(cache_path).encode()
-    _check(lib().shf_autotune(h, path, out, 3 * nclasses), h, "shf_autotune")
-    triples = [(out[3 * c], out[3 * c + 1], out[3 * c + 2]) for c in range(nclasses)]
-    return [t for t in triples if t[0] > 0]
+    _check(lib().shf_autotune(h, path, out, 2 * nclasses), h, "shf_autotune")
+    pairs = [(out[2 * c], out[2 * c + 1]) for c in range(nclasses)]
+    return [t for t in pairs if t[0] > 0]
 
 
 def shf_structure_factor(h, nbins=0):

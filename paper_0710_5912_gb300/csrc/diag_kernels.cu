@@ -82,16 +82,41 @@ __device__ __forceinline__ unsigned nonfinite_bit(float x) {
 }
 
 // FP32 fields: out[3*cta + 0..2] = (sum, compensation, non-finite count) over
-// this CTA's grid-stride share of f.  A thread reads 16-byte vectors, two per
-// group of eight values (one from each of two consecutive grid strides, so
-// every load is coalesced), and sums a group exactly as a float pair by a tree
-// of TwoSums: the head goes into a double accumulator by one plain addition
-// (the only double-precision operation per eight values), the tails into a
-// float one.  Each double addition rounds at most half an ulp of the thread's
-// running sum, so the thread total is within a few 1e-16 of its exact sum
-// relative to its magnitude; threads and CTAs are then combined with
-// Neumaier's compensated sum.  Fixed order throughout: for one field and
-// launch shape the result is always the same bits.
+// this CTA's grid-stride share of f.  A thread reads 16-byte vectors, eight
+// per group of 32 values (one from each of eight consecutive grid strides, all
+// in flight at once), and adds each group with a tree of Knuth's TwoSum in
+// FP32: the group's rounded sum goes into a double accumulator (one FP64
+// addition per 32 values, the FP64 pipe being narrow on this part) and the
+// exact rounding errors of the tree into a float one.  Each double addition
+// rounds at most half an ulp of the thread's running sum, so the thread total
+// is within a few 1e-16 of its exact sum relative to its magnitude; threads
+// and CTAs are then combined with Neumaier's compensated sum.  Fixed order
+// throughout: for one field and launch shape the result is always the same
+// bits.
+constexpr int kMassVec = 8;   // 16-byte vectors per group
+__device__ __forceinline__ float mass_group(const float4 (&v)[kMassVec], float& err, unsigned& bad) {
+  float s[2 * kMassVec];
+  float e = 0.f;
+#pragma unroll
+  for (int k = 0; k < kMassVec; ++k) {
+    bad |= nonfinite_bit(v[k].x) | nonfinite_bit(v[k].y) | nonfinite_bit(v[k].z) | nonfinite_bit(v[k].w);
+    float e0, e1;
+    s[2 * k] = two_sum(v[k].x, v[k].y, e0);
+    s[2 * k + 1] = two_sum(v[k].z, v[k].w, e1);
+    e += e0 + e1;
+  }
+#pragma unroll
+  for (int w = 2 * kMassVec; w > 1; w >>= 1) {        // pairwise tree, fixed order
+#pragma unroll
+    for (int k = 0; k < w / 2; ++k) {
+      float ek;
+      s[k] = two_sum(s[2 * k], s[2 * k + 1], ek);
+      e += ek;
+    }
+  }
+  err += e;
+  return s[0];
+}
 __global__ void __launch_bounds__(256) k_mass_partials_f32(const float* __restrict__ f, long long count,
                                                            double* __restrict__ out) {
   __shared__ double sh[2 * 2 * 32];
@@ -103,19 +128,13 @@ __global__ void __launch_bounds__(256) k_mass_partials_f32(const float* __restri
   const long long n4 = (reinterpret_cast<uintptr_t>(f) & 15) == 0 ? count / 4 : 0;
   const float4* f4 = reinterpret_cast<const float4*>(f);
   long long e = tid;
-  for (; e + stride < n4; e += 2 * stride) {
-    const float4 a = __ldcs(f4 + e), b = __ldcs(f4 + e + stride);
-    bad |= nonfinite_bit(a.x) | nonfinite_bit(a.y) | nonfinite_bit(a.z) | nonfinite_bit(a.w) |
-           nonfinite_bit(b.x) | nonfinite_bit(b.y) | nonfinite_bit(b.z) | nonfinite_bit(b.w);
-    float e0, e1, e2, e3, e4, e5, e6;
-    const float s01 = two_sum(a.x, a.y, e0), s23 = two_sum(a.z, a.w, e1);
-    const float s45 = two_sum(b.x, b.y, e2), s67 = two_sum(b.z, b.w, e3);
-    const float s03 = two_sum(s01, s23, e4), s47 = two_sum(s45, s67, e5);
-    const float h = two_sum(s03, s47, e6);
-    acc += (double)h;
-    tail += (((e0 + e1) + (e2 + e3)) + (e4 + e5)) + e6;
+  for (; e + (kMassVec - 1) * stride < n4; e += kMassVec * stride) {
+    float4 v[kMassVec];
+#pragma unroll
+    for (int k = 0; k < kMassVec; ++k) v[k] = __ldcs(f4 + e + k * stride);
+    acc += (double)mass_group(v, tail, bad);
   }
-  if (e < n4) {
+  for (; e < n4; e += stride) {                        // the last partial group
     const float4 a = __ldcs(f4 + e);
     bad |= nonfinite_bit(a.x) | nonfinite_bit(a.y) | nonfinite_bit(a.z) | nonfinite_bit(a.w);
     float e0, e1, e2;

@@ -178,7 +178,7 @@ int sm_count() {
 template <class T>
 LaunchCfg persistent_cfg(int kind, int nfft, int max_inst, int items, size_t inst_bytes, int nmem, int P = kP) {
   LaunchCfg c{};
-  const bool fwd = kind == KIND_STAGE1 || kind == KIND_ROWFWD_G;
+  const bool fwd = kind == KIND_STAGE1 || kind == KIND_STAGE2;
   const bool rows = fwd || kind == KIND_ROWINV_PHI || kind == KIND_ROWINV_FLOW;
   const int cta = (rows || P == 16) ? rowfwd_cta_threads(P) : 512;   // FP32 column passes: 16 points, 256 threads
   const int Tf = nfft / P;
@@ -203,21 +203,18 @@ LaunchCfg persistent_cfg(int kind, int nfft, int max_inst, int items, size_t ins
 }
 
 // The tuning knobs of a size class: points per thread of the fused stage-1
-// row pass (8 or 16; FP64: 8), of the g row pass (FP32: 16, whose radix-16
-// first stage yields the force's low modes; FP64: 8) and the stage-2 stencil
-// tile height (16 or 32, at most ny).  Zero means "the default".
+// row pass (8 or 16; FP64: 8) and of the fused stage-2 row pass (FP32: 16,
+// whose radix-16 first stage yields the force's low modes; FP64: 8).  Zero
+// means "the default".
 struct Tune {
   int stage1_points = 0;
-  int rowfwd_g_points = 0;
-  int stencil_rows = 0;
+  int stage2_points = 0;
 };
 
 template <class T>
-Tune resolved(const SizeClass& cl, Tune t) {
+Tune resolved(const SizeClass&, Tune t) {
   if (t.stage1_points == 0 || sizeof(T) == 8) t.stage1_points = rowfwd_default_points<T>();
-  t.rowfwd_g_points = rowfwd_default_points<T>();
-  const int maxrows = cl.ny < 32 ? cl.ny : 32;
-  if (t.stencil_rows == 0 || t.stencil_rows > maxrows) t.stencil_rows = maxrows;
+  t.stage2_points = rowfwd_default_points<T>();
   return t;
 }
 
@@ -226,19 +223,10 @@ void configure_class_t(SizeClass& cl, Tune tune) {
   tune = resolved<T>(cl, tune);
   const size_t R = sizeof(T), Cx = 2 * R;
   const int nx = cl.nx, ny = cl.ny, nmem = (int)cl.members.size();
-  // stage-2 stencil tiles of TX = min(nx, 128) by TY rows, 4 x 4 outputs per thread
-  const int TX = nx < 128 ? nx : 128, TY = tune.stencil_rows;
-  LaunchCfg st{};
-  st.grid_x = nx / TX;
-  st.grid_y = ny / TY;
-  st.threads = (TX / 4) * (TY / 4);
-  st.variant = TY;
-  st.smem = stencil2_smem_bytes(TX, TY, R);
-  cl.cfg[KIND_STENCIL2] = st;
   cl.cfg[KIND_STAGE1] = persistent_cfg<T>(KIND_STAGE1, nx, ny / 2, ny / 2, 2 * stage1_inst_bytes(nx, R), nmem,
                                            tune.stage1_points);
-  cl.cfg[KIND_ROWFWD_G] = persistent_cfg<T>(KIND_ROWFWD_G, nx, ny / 2, ny / 2, rowfwd_inst_bytes(nx, R), nmem,
-                                             tune.rowfwd_g_points);
+  cl.cfg[KIND_STAGE2] = persistent_cfg<T>(KIND_STAGE2, nx, ny / 2, ny / 2, rowfwd_inst_bytes(nx, R), nmem,
+                                           tune.stage2_points);
   // column items: single mode columns with 16 points per thread (FP32), or
   // whole 16-byte chunks of one complex double with 8 (FP64)
   const int ncol_items = nx / 2;
@@ -293,7 +281,6 @@ MemberDesc make_desc(const shf_grid* o, const Member& m) {
   d.omega_star = m.omega_star;
   d.nyq_phi = m.nyq;
   d.nyq_omega = static_cast<char*>(m.nyq) + (size_t)m.ny * (o->precision == SHF_FP64 ? 8 : 4);
-  d.gbuf = m.phi_star;   // g is formed after phi^{n+1}, when phi* is no longer needed
   d.st = m.d_st;
   d.a = m.a; d.b = m.b; d.kappa = m.kappa; d.M = m.M; d.eta = m.eta; d.rho = m.rho;
   d.gdot = m.gdot; d.dt = m.dt; d.dx = m.dx;
@@ -600,7 +587,7 @@ void enqueue_state_init(shf_grid* o) {
     for (auto& cl : o->classes) {
       const int nm = (int)cl.members.size();
       launch_row_kernel<float>(KIND_ROWFWD_OMEGA, cl.d_desc, nm, cl.log2nx, cl.log2ny,
-                               static_cast<const float2*>(o->d_twr), cl.cfg[KIND_ROWFWD_G], o->stream);
+                               static_cast<const float2*>(o->d_twr), cl.cfg[KIND_STAGE2], o->stream);
       launch_col_kernel<float>(KIND_COLPASS_WINIT, cl.d_desc, nm, cl.log2nx, cl.log2ny,
                                static_cast<const float2*>(o->d_twr), cl.cfg[KIND_COLPASS_FLOW], o->stream);
     }
@@ -792,7 +779,7 @@ std::string tune_key(const shf_grid* o, const SizeClass& cl) {
 }
 
 // cache file: a JSON object, one entry per line:
-//   "NXxNY:fp32:inertial": {"stage1_points": 16, "rowfwd_g_points": 16, "stencil_rows": 32},
+//   "NXxNY:fp32:inertial": {"stage1_points": 16, "stage2_points": 16},
 std::map<std::string, Tune> read_tune_cache(const char* path) {
   std::map<std::string, Tune> m;
   if (!path) return m;
@@ -802,8 +789,8 @@ std::map<std::string, Tune> read_tune_cache(const char* path) {
   while (std::fgets(line, sizeof(line), f)) {
     char key[256];
     Tune t;
-    if (std::sscanf(line, " \"%255[^\"]\": {\"stage1_points\": %d, \"rowfwd_g_points\": %d, \"stencil_rows\": %d",
-                    key, &t.stage1_points, &t.rowfwd_g_points, &t.stencil_rows) == 4)
+    if (std::sscanf(line, " \"%255[^\"]\": {\"stage1_points\": %d, \"stage2_points\": %d", key, &t.stage1_points,
+                    &t.stage2_points) == 3)
       m[key] = t;
   }
   std::fclose(f);
@@ -816,9 +803,8 @@ bool write_tune_cache(const char* path, const std::map<std::string, Tune>& m) {
   std::fprintf(f, "{\n");
   size_t i = 0;
   for (const auto& kv : m) {
-    std::fprintf(f, "  \"%s\": {\"stage1_points\": %d, \"rowfwd_g_points\": %d, \"stencil_rows\": %d}%s\n",
-                 kv.first.c_str(), kv.second.stage1_points, kv.second.rowfwd_g_points, kv.second.stencil_rows,
-                 ++i < m.size() ? "," : "");
+    std::fprintf(f, "  \"%s\": {\"stage1_points\": %d, \"stage2_points\": %d}%s\n", kv.first.c_str(),
+                 kv.second.stage1_points, kv.second.stage2_points, ++i < m.size() ? "," : "");
   }
   std::fprintf(f, "}\n");
   return std::fclose(f) == 0;
@@ -850,8 +836,8 @@ int time_kinds(shf_grid* o, SizeClass& cl, const int* kinds, int nk, float* ms) 
 
 // Time the candidate values of each knob on the class's own buffers.  Only
 // kinds that write scratch (the stage-1 pass: phi*, omega*, the x-spectral
-// buffers; the stage-2 stencil: g) run, so the state (phi, psi, omega,
-// omega_hat, step) is untouched.
+// buffers) run, so the state (phi, psi, omega, omega_hat, step) is
+// untouched.
 template <class T>
 int tune_class(shf_grid* o, SizeClass& cl, Tune* best) {
   Tune t = resolved<T>(cl, Tune{});
@@ -868,22 +854,6 @@ int tune_class(shf_grid* o, SizeClass& cl, Tune* best) {
       if (P == 8 || ms < bestms) {
         bestms = ms;
         t.stage1_points = P;
-      }
-    }
-  }
-  if (cl.ny >= 32) {
-    const int st[1] = {KIND_STENCIL2};
-    float bestms = 0.f;
-    for (int TY : {16, 32}) {
-      Tune c = t;
-      c.stencil_rows = TY;
-      configure_class_t<T>(cl, c);
-      float ms = 0.f;
-      const int rc = time_kinds<T>(o, cl, st, 1, &ms);
-      if (rc) return rc;
-      if (TY == 16 || ms < bestms) {
-        bestms = ms;
-        t.stencil_rows = TY;
       }
     }
   }
@@ -1323,10 +1293,9 @@ int shf_autotune(shf_grid* g, const char* cache_path, int* choices, int nchoices
     configure_class(cl, g->precision, t);
     if (g->precision == SHF_FP64) t = resolved<double>(cl, t);
     else t = resolved<float>(cl, t);
-    if ((int)(3 * c + 2) < nchoices) {
-      choices[3 * c] = t.stage1_points;
-      choices[3 * c + 1] = t.rowfwd_g_points;
-      choices[3 * c + 2] = t.stencil_rows;
+    if ((int)(2 * c + 1) < nchoices) {
+      choices[2 * c] = t.stage1_points;
+      choices[2 * c + 1] = t.stage2_points;
     }
   }
   if (g->graph) {                                       // re-captured with the new launch shapes

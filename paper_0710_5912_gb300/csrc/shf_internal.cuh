@@ -35,7 +35,6 @@ struct MemberDesc {
   void* omega_star;  // omega* (real, already remapped at a wrap)
   void* nyq_phi;     // per row: the real Nyquist coefficient of phi*'s row DFT
   void* nyq_omega;   // per row: the same for omega*
-  void* gbuf;        // g = -F/rho (or -F/eta), real; shares phi*'s storage (phi* is dead by then)
   // FP32 members: vorticity carried in 2D spectral form and low modes of the
   // force computed apart (see step_cols.cu).  w_hat: the 2D DFT of omega
   // (unnormalised), nx/2 x ny complex in the column-chunk layout of the
@@ -101,11 +100,6 @@ __device__ __forceinline__ void strain_dev(long long n, double gdot, double dt, 
 // one x-spectral chunk column of each input field plus the buffer; rowinv
 // stages the 32-byte chunks of a row pair (nx complex) plus the buffer.
 __host__ __device__ constexpr size_t round128(size_t b) { return (b + 127) & ~(size_t)127; }
-// Stage-2 stencil tiles (dynamic shared memory): a (TY + 4) x (TX + 12) phi
-// tile and a (TY + 2) x (TX + 12) mu tile.
-__host__ __device__ constexpr size_t stencil2_smem_bytes(int TX, int TY, size_t real_bytes) {
-  return (size_t)(2 * TY + 6) * (TX + 12) * real_bytes;
-}
 __host__ __device__ constexpr size_t rowfwd_inst_bytes(int nx, size_t real_bytes) {
   return round128(2 * (size_t)nx * real_bytes + (size_t)padded_len(nx) * 2 * real_bytes);
 }
@@ -156,12 +150,11 @@ enum StepKind {
   KIND_STAGE1 = 0,        // stage-1 stencil fused with the row transforms of phi*, f, omega*
   KIND_COLPASS_PHI = 1,
   KIND_ROWINV_PHI = 2,
-  KIND_STENCIL2 = 3,
-  KIND_ROWFWD_G = 4,
-  KIND_LOWMODE = 5,
-  KIND_COLPASS_FLOW = 6,
-  KIND_ROWINV_FLOW = 7,
-  KIND_COUNT = 8
+  KIND_STAGE2 = 3,        // stage-2 stencil fused with the row transform of g (+ its low row modes)
+  KIND_LOWMODE = 4,
+  KIND_COLPASS_FLOW = 5,
+  KIND_ROWINV_FLOW = 6,
+  KIND_COUNT = 7
 };
 // Launches outside the step: the 2D transform of omega into w_hat (after
 // the fields were set from outside), as a row pass and a column pass.
@@ -172,7 +165,7 @@ struct LaunchCfg {
   int threads;
   size_t smem;          // dynamic shared memory bytes
   int inst_per_cta;     // transform instances per CTA (persistent kinds)
-  int variant;          // rows: points per thread (8, 16); stage-2 stencil: tile rows (16, 32);
+  int variant;          // rows: points per thread (8, 16);
                         // FP32 flow column pass: members' regime (1 inertial, 2 Stokes, 3 mixed)
 };
 

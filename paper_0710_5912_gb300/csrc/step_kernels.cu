@@ -1,49 +1,48 @@
 // Kernels of one time step (Appendix B of arXiv:0710.5912), templated on the
-// working precision T (float or double).  A step is eight launches per grid
-// size:
+// working precision T (float or double).  A step is seven launches per grid
+// size (six for FP64):
 //
-//   stencil1     item 1 + item 2's advection at s = s^n (Eq. advective with the
-//                Eq. p1y stencils): phi* = phi - dt J(psi, phi) and omega* =
-//                omega - dt J(psi, omega), real (FP32 inertial members: the
-//                increment -dt J(psi, omega) alone, see step_cols.cu); omega*
-//                is written at the relabelled positions when the strain wraps
-//                during the step.
-//   rowfwd_phi   row (x) transforms of the phi*, f = phi^3 and omega* row
-//                pairs -> x-spectral buffers, plus each row's real Nyquist
-//                coefficient of phi* and omega*.
+//   stage1       item 1 + item 2's advection at s = s^n (Eq. advective with the
+//                Eq. p1y stencils), fused with the row (x) transforms of what
+//                it makes: phi* = phi - dt J(psi, phi) (written out, the base
+//                of phi's increment) -> xs_phi; f = phi^3 -> xs_f; omega* =
+//                omega - dt J(psi, omega), or for FP32 inertial members the
+//                increment -dt J(psi, omega) alone (omega is carried as its 2D
+//                transform w_hat, step_cols.cu) -> xs_w, at the relabelled
+//                positions when the strain wraps during the step
+//                (k_stage1_rows, step_rows.cu).
 //   colpass_phi  column (y) transforms of phi*, f; the Cahn-Hilliard update of
 //                item 1 in the paper's increment form
 //                  phi^{n+1} = phi* + (1 + D4/2)^-1 (-D2 phi* - D4 phi* + D2 f),
 //                Nyquist modes of phi^{n+1} zeroed; the increment back along y.
 //   rowinv_phi   phi^{n+1} = phi* + row inverse of the increment (minus phi*'s
 //                Nyquist column), written at the relabelled positions at a wrap.
-//   stencil2     mu = -a phi + b phi^3 - kappa lap_c phi and the body-force curl
+//   stage2       mu = -a phi + b phi^3 - kappa lap_c phi and the body-force curl
 //                F = d_x phi d_y mu - d_y phi d_x mu at s = s^{n+1} (Eq. G);
-//                g = -F/rho, or -F/eta for Stokes, real.
-//   rowfwd_g     row transforms of g row pairs (FP32: plus the low row modes
-//                of g with compensated sums).
-//   lowmode      FP32: the column DFT of those low row modes.
-//   colpass_flow column transforms; Crank-Nicolson vorticity update in increment
-//                form omega^{n+1} = omega* + (1 - C/2)^-1 (C omega* + g) and the
-//                Poisson solve psi = omega / k^2 (items 2-3), or the Stokes solve
+//                g = -F/rho, or -F/eta for Stokes, computed straight into the
+//                row transform of g (k_rowfwd mode 1; FP32 inertial: plus the
+//                low row modes of g with compensated sums).
+//   lowmode      FP32: the column DFT of the low row modes of g (for Stokes
+//                members, first the exact low row modes, k_lowrows_exact
+//                below).
+//   colpass_flow column transforms; Crank-Nicolson vorticity update
+//                omega^{n+1} = omega* + (dt g - 2C omega*) / (1 + C) with
+//                C = dt (eta / rho) k^2 / 2, and the Poisson solve
+//                psi = omega / k^2 (items 2-3), or the Stokes solve
 //                psi = g / k^4; inverse column transforms.
-//   rowinv_flow  psi rows, and omega^{n+1} = omega* + row inverse of the
-//                increment; advances the step counter.
+//   rowinv_flow  psi rows and omega^{n+1}; advances the step counter.
 //
 // Transforming only the increments keeps the FP32 rounding of a step
 // proportional to the change of the field instead of to the field itself.
 //
-// This file holds the stencils and the launch dispatch; the transform kernels
-// are in step_rows.cu and step_cols.cu (compiled per transform length).
-//
-// Execution: the FP32 stage-1 stencil (nx >= 128) streams row strips through
-// registers; the other stencils run on 2D tiles, 4 x 4 outputs per thread; the
-// transform kernels are persistent -- every instance walks its work items (row
-// pairs or column chunks) with a grid stride and, while transforming one item,
-// streams the next item's input into a shared-memory staging buffer with
-// cp.async, so the loads in flight hold shared memory rather than registers.
-// The FFT keeps 8 (or, in the FP32 row passes, 16) points per thread in
-// registers (fft_block.cuh).
+// This file holds the exact low-mode kernel of the Stokes force, the state
+// seeding and the launch dispatch; the transform kernels (with the fused
+// stencils) are in step_rows.cu and step_cols.cu, compiled per transform
+// length.  The transform kernels are persistent -- every instance walks its
+// work items (row pairs or column chunks) with a grid stride and, while
+// transforming one item, streams the next item's input into shared memory
+// (cp.async) or L2 (bulk prefetch).  The FFT keeps 8 (FP64) or 16 (FP32)
+// points per thread in registers (fft_block.cuh).
 //
 // Layout: real fields ny x nx row-major.  x-spectral buffers hold, for each row
 // j, the modes m = 0..nx/2-1 of the row's real DFT (the Nyquist column is
@@ -59,144 +58,6 @@ namespace shf {
 __global__ void k_step_state_init(const MemberDesc* __restrict__ descs, int nmem) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r < nmem) step_state_set(descs[r], descs[r].st->n);
-}
-
-// ============================================================== stencils
-// 2D tiles of TX x TY outputs (TX = min(nx, 128), TY = min(ny, 32)); each
-// thread makes a 4 x 4 block of outputs (4 consecutive x in 4 rows), reading
-// its stencil rows from the shared tile with 16-byte loads.  The sign of s
-// selects one of two compiled bodies (the diagonal of Eq. p1y lies on one side).
-
-// Fill rows [0, H) of NF tiles (tile column c <-> x0 - OFF + c, OFF = 2 or 6,
-// width TX + 2 OFF) from NF fields at rows y0 - HY + r (periodic), with
-// asynchronous copies (all of a thread's copies are in flight at once) of two
-// reals each: the interior in pairs, the OFF halo columns on each side as
-// pairs.  Returns after the copies have landed (this thread's; the caller
-// then synchronises the CTA).
-template <class T>
-__device__ __forceinline__ void cp_async_pair(T* dst, const T* src) {
-  if (sizeof(T) == 4) cp_async8(dst, src);
-  else cp_async16(dst, src);
-}
-template <class T, int TX, int OFF, int H, int NF>
-__device__ __forceinline__ void fill_tiles(T* tile, const T* const* src, int x0, int yb, int log2nx, int my,
-                                           int tid, int nthr) {
-  constexpr int QX = TX / 4, W = TX + 2 * OFF, HP = OFF / 2;   // HP halo pairs per side
-  constexpr int SLOTS = QX + 2 * HP;
-  const int mx = (1 << log2nx) - 1;
-  for (int e = tid; e < NF * H * SLOTS; e += nthr) {
-    const int f = e / (H * SLOTS);
-    const int rem = e - f * (H * SLOTS);
-    const int r = rem / SLOTS, k = rem - r * SLOTS;
-    const T* row = src[f] + ((size_t)((yb + r) & my) << log2nx);
-    T* trow = tile + ((size_t)f * H + r) * W;
-    if (k < QX) {
-      const T* g = row + x0 + 4 * k;
-      T* d = trow + OFF + 4 * k;
-      cp_async_pair(d, g);
-      cp_async_pair(d + 2, g + 2);
-    } else {
-      const int h = k - QX;                               // 0 .. 2 HP - 1
-      const int side = h / HP, j = h - side * HP;         // left (0) or right (1) halo, pair j
-      const int c = side == 0 ? 2 * j : OFF + TX + 2 * j;
-      const int x = (x0 - OFF + c) & mx;                  // even, so the pair is contiguous
-      cp_async_pair(trow + c, row + x);
-    }
-  }
-  cp_async_commit();
-  cp_async_wait_all();
-}
-
-// stage-2 stencil: mu = -a phi + b phi^3 - kappa L_s phi (Appendix B item 2:
-// 3-point second differences, 4-point cross difference) on a tile with halo
-// x +-2, y +-1 from phi (halo x +-6 loaded, y +-2), then
-// g = c_force (D_x phi D_y^s mu - D_y^s phi D_x mu) (Eqs. vortNum, G).
-template <bool NEG, class T, int TX, int TY>
-__device__ __forceinline__ void stencil2_body(const MemberDesc& D, const T* tp, T* tm, const Shear<T>& sc, int x0,
-                                              int y0, int log2nx) {
-  constexpr int QX = TX / 4, W = TX + 12, HP = TY + 4, HM = TY + 2;
-  constexpr int NQ = QX + 1;                  // mu quads per row: tile cols 4 .. TX + 7
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const T a = (T)D.a, b = (T)D.b, kappa = (T)D.kappa;
-  const T ih2 = (T)D.inv_h2, i4h2 = (T)D.inv_4h2, inv2h = (T)D.inv_2h;
-  const T cxx = T(1) + sc.s * sc.s, cxy = T(2) * sc.s;
-  // kappa and the difference scalings folded into the three Laplacian weights
-  const T kxx = kappa * cxx * ih2, kxy = kappa * cxy * i4h2, kyy = kappa * ih2;
-  // mu tile row rm <-> y0 - 1 + rm <-> phi tile row rm + 1; mu quad at tile col 4 (k + 1).
-  // Work unit: one quad column k over RPT consecutive mu rows, with a three-row
-  // window of phi (one new phi row per mu row).
-  constexpr int NT = QX * (TY / 4);                    // threads of the CTA
-  constexpr int RG = NT / NQ;                          // row groups
-  constexpr int RPT = (HM + RG - 1) / RG;              // mu rows per unit
-  if (tid < NQ * RG) {
-    const int k = tid % NQ, rg = tid / NQ;
-    const int c = 4 * (k + 1);
-    const int r0 = rg * RPT;
-    Six<T> Dn = ld6(tp + r0 * W + c), Cn = ld6(tp + (r0 + 1) * W + c);
-#pragma unroll
-    for (int i = 0; i < RPT; ++i) {                     // a fixed trip count, so the window stays in registers
-      const int rm = r0 + i;
-      if (rm >= HM) break;
-      const Six<T> Un = ld6(tp + (rm + 2) * W + c);
-      T m[4];
-#pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        const T pc = Cn.v[p + 1];
-        const T sxx = Cn.v[p + 2] - T(2) * pc + Cn.v[p];          // unscaled second differences
-        const T syy = Un.v[p + 1] - T(2) * pc + Dn.v[p + 1];
-        const T sxy = Un.v[p + 2] - Dn.v[p + 2] - Un.v[p] + Dn.v[p];
-        const T klap = kxx * sxx - kxy * sxy + kyy * syy;          // kappa L_s phi
-        m[p] = pc * (b * (pc * pc) - a) - klap;
-      }
-      st4(tm + rm * W + c, m[0], m[1], m[2], m[3]);
-      Dn = Cn;
-      Cn = Un;
-    }
-  }
-  __syncthreads();
-  const int q = tid % QX, g = tid / QX;
-  const T cf = (T)D.c_force;
-  T* gout = static_cast<T*>(D.gbuf);
-  const int x = x0 + 4 * q;
-  // the 8-wide rows of output block (cols x - 2 .. x + 5) start at tile col 4 q + 4;
-  // output row y0 + 4 g + o is phi tile row 4 g + 2 + o and mu tile row 4 g + 1 + o
-  const T* pcol = tp + 4 * q + 4;
-  const T* mcol = tm + 4 * q + 4;
-  Row8<T> pD = ld8(pcol + (4 * g + 1) * W), pC = ld8(pcol + (4 * g + 2) * W);
-  Row8<T> mD = ld8(mcol + (4 * g) * W), mC = ld8(mcol + (4 * g + 1) * W);
-#pragma unroll
-  for (int o = 0; o < 4; ++o) {
-    const int y = y0 + 4 * g + o;
-    const Row8<T> pU = ld8(pcol + (4 * g + 3 + o) * W), mU = ld8(mcol + (4 * g + 2 + o) * W);
-    T dxp[4], dyp[4], dxm[4], dym[4];
-    grad4<NEG>(pU, pC, pD, sc.w0, sc.w1, inv2h, dxp, dyp);
-    grad4<NEG>(mU, mC, mD, sc.w0, sc.w1, inv2h, dxm, dym);
-    T r[4];
-#pragma unroll
-    for (int p = 0; p < 4; ++p) r[p] = cf * diff_of_products(dxp[p], dym[p], dyp[p], dxm[p]);
-    st4(gout + ((size_t)y << log2nx) + x, r[0], r[1], r[2], r[3]);
-    pD = pC;
-    pC = pU;
-    mD = mC;
-    mC = mU;
-  }
-}
-
-template <class T, int TX, int TY>
-__global__ void __launch_bounds__(256) k_stencil2(const MemberDesc* __restrict__ descs, int log2nx, int log2ny) {
-  constexpr int W = TX + 12, HP = TY + 4;
-  extern __shared__ __align__(16) unsigned char smem_raw[];   // stencil2_smem_bytes
-  T* tp = reinterpret_cast<T*>(smem_raw);                     // phi tile, HP x W
-  T* tm = tp + HP * W;                                        // mu tile, (TY + 2) x W
-  const MemberDesc& D = descs[blockIdx.z];
-  const int my = (1 << log2ny) - 1;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-  const Shear<T> sc(*D.st, true);                       // s^{n+1}
-  const T* src[1] = {static_cast<const T*>(D.phi)};
-  fill_tiles<T, TX, 6, HP, 1>(tp, src, x0, y0 - 2, log2nx, my, threadIdx.x, blockDim.x);
-  __syncthreads();
-  if (sc.d > 0) stencil2_body<true, T, TX, TY>(D, tp, tm, sc, x0, y0, log2nx);
-  else stencil2_body<false, T, TX, TY>(D, tp, tm, sc, x0, y0, log2nx);
 }
 
 // ======================================= exact low row modes of the Stokes force
@@ -391,45 +252,10 @@ void launch_step_state_init(const MemberDesc* d, int nmem, cudaStream_t st) {
   k_step_state_init<<<(nmem + 127) / 128, 128, 0, st>>>(d, nmem);
 }
 
-// stencil tiles: TX = min(nx, 128) columns, TY = min(ny, 32) rows,
-// (TX / 4) (TY / 4) threads
-template <class T, int TX, int TY>
-void launch_stencil_t(const MemberDesc* d, int nmem, int log2nx, int log2ny, const LaunchCfg& c, cudaStream_t st) {
-  const dim3 grid(c.grid_x, c.grid_y, nmem);
-  k_stencil2<T, TX, TY><<<grid, c.threads, c.smem, st>>>(d, log2nx, log2ny);
-}
-template <class T, int TX, int TY>
-void stencil_smem_limits_t(int lim) {
-  cudaFuncSetAttribute(k_stencil2<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-}
-template <class T, int TY>
-void stencil_smem_limits_ty(int lim) {
-  stencil_smem_limits_t<T, 16, TY>(lim);
-  stencil_smem_limits_t<T, 32, TY>(lim);
-  stencil_smem_limits_t<T, 64, TY>(lim);
-  stencil_smem_limits_t<T, 128, TY>(lim);
-}
-template <class T, int TY>
-void launch_stencil_ty(const MemberDesc* d, int nmem, int log2nx, int log2ny, const LaunchCfg& c, cudaStream_t st) {
-  switch (log2nx) {
-    case 4: launch_stencil_t<T, 16, TY>(d, nmem, log2nx, log2ny, c, st); break;
-    case 5: launch_stencil_t<T, 32, TY>(d, nmem, log2nx, log2ny, c, st); break;
-    case 6: launch_stencil_t<T, 64, TY>(d, nmem, log2nx, log2ny, c, st); break;
-    default: launch_stencil_t<T, 128, TY>(d, nmem, log2nx, log2ny, c, st); break;
-  }
-}
-// the stage-2 stencil; the tile height TY (16 or 32, at most ny) is the launch's variant
-template <class T>
-void launch_stencil(const MemberDesc* d, int nmem, int log2nx, int log2ny, const LaunchCfg& c, cudaStream_t st) {
-  if (c.variant == 32) launch_stencil_ty<T, 32>(d, nmem, log2nx, log2ny, c, st);
-  else launch_stencil_ty<T, 16>(d, nmem, log2nx, log2ny, c, st);
-}
-
 template <class T>
 void launch_step_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int log2ny, const cplx<T>* tw,
                         const LaunchCfg& c, cudaStream_t st) {
   switch (kind) {
-    case KIND_STENCIL2: launch_stencil<T>(d, nmem, log2nx, log2ny, c, st); break;
     case KIND_COLPASS_PHI:
     case KIND_COLPASS_FLOW: launch_col_kernel<T>(kind, d, nmem, log2nx, log2ny, tw, c, st); break;
     default: launch_row_kernel<T>(kind, d, nmem, log2nx, log2ny, tw, c, st); break;
@@ -449,8 +275,6 @@ void set_step_smem_limits() {
   const int lim = 220 * 1024;   // dynamic part; leaves room for static shared memory
   set_row_smem_limits<T>(lim);
   set_col_smem_limits<T>(lim);
-  stencil_smem_limits_ty<T, 16>(lim);
-  stencil_smem_limits_ty<T, 32>(lim);
   if (sizeof(T) == 4) cudaFuncSetAttribute(k_lowrows_exact, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
 }
 

@@ -130,13 +130,99 @@ __device__ __forceinline__ void low_row_reduce(float* Zb, int t, const MemberDes
   __syncthreads();
 }
 
+// ===================================================== stage-2 stencil of a row pair
+// mu = -a phi + b phi^3 - kappa L_s phi (Appendix B item 2: 3-point second
+// differences, the 4-point cross difference) and the body-force curl
+// g = c_force (D_x phi D_y^s mu - D_y^s phi D_x mu) at s = s^{n+1} (Eqs.
+// vortNum, G), for rows j0, j0 + 1, written as two real rows into buf.  A
+// thread takes columns x0 .. x0 + 3 (x0 = 4k) and walks phi's rows j0 - 2 ..
+// j0 + 3 straight from global memory (the item's rows were prefetched into
+// L2), forming mu of rows j0 - 1 .. j0 + 2 at x0 - 2 .. x0 + 5 as each phi
+// row arrives; only three phi rows and three mu rows are live at a time.
+
+// columns x0 - 4 .. x0 + 7 of a global row (x0 a multiple of 4), periodic
+template <class T>
+struct Row12 {
+  T v[12];
+};
+template <class T>
+__device__ __forceinline__ Row12<T> ld12_row(const T* row, int x0, int mx) {
+  const Quad<T> a = ldg4(row + ((x0 - 4) & mx)), b = ldg4(row + x0), c = ldg4(row + ((x0 + 4) & mx));
+  return Row12<T>{{a.v[0], a.v[1], a.v[2], a.v[3], b.v[0], b.v[1], b.v[2], b.v[3], c.v[0], c.v[1], c.v[2], c.v[3]}};
+}
+// the middle eight (x0 - 2 .. x0 + 5)
+template <class T>
+__device__ __forceinline__ Row8<T> mid8(const Row12<T>& r) {
+  return Row8<T>{{r.v[2], r.v[3], r.v[4], r.v[5], r.v[6], r.v[7], r.v[8], r.v[9]}};
+}
+template <class T>
+struct MuConsts {
+  T a, b, kxx, kxy, kyy;
+};
+// mu at x0 - 2 .. x0 + 5 of the row whose phi is C (U above, Dn below)
+template <class T>
+__device__ __forceinline__ Row8<T> mu8(const Row12<T>& U, const Row12<T>& C, const Row12<T>& Dn,
+                                       const MuConsts<T>& k) {
+  Row8<T> m;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const T pc = C.v[c + 2];
+    const T sxx = C.v[c + 3] - T(2) * pc + C.v[c + 1];          // unscaled second differences
+    const T syy = U.v[c + 2] - T(2) * pc + Dn.v[c + 2];
+    const T sxy = U.v[c + 3] - Dn.v[c + 3] - U.v[c + 1] + Dn.v[c + 1];
+    const T klap = k.kxx * sxx - k.kxy * sxy + k.kyy * syy;      // kappa L_s phi
+    m.v[c] = pc * (k.b * (pc * pc) - k.a) - klap;
+  }
+  return m;
+}
+template <bool NEG, class T>
+__device__ __forceinline__ void stage2_pair(const MemberDesc& D, const T* __restrict__ phi, T* buf, int j0,
+                                            int log2nx, int my, const Shear<T>& sc, int t, int Tf) {
+  const int nx = 1 << log2nx, mx = nx - 1;
+  const T cxx = T(1) + sc.s * sc.s, cxy = T(2) * sc.s;
+  const T kappa = (T)D.kappa;
+  const MuConsts<T> k{(T)D.a, (T)D.b, kappa * cxx * (T)D.inv_h2, kappa * cxy * (T)D.inv_4h2, kappa * (T)D.inv_h2};
+  const T inv2h = (T)D.inv_2h, cf = (T)D.c_force;
+  auto row = [&](int j) { return phi + ((size_t)(j & my) << log2nx); };
+  for (int q = t; q < (nx >> 2); q += Tf) {
+    const int x0 = 4 * q;
+    Row12<T> p0 = ld12_row(row(j0 - 2), x0, mx), p1 = ld12_row(row(j0 - 1), x0, mx), p2 = ld12_row(row(j0), x0, mx);
+    Row12<T> p3 = ld12_row(row(j0 + 1), x0, mx);
+    const Row8<T> m0 = mu8(p2, p1, p0, k);             // mu rows j0 - 1, j0, j0 + 1, j0 + 2
+    Row8<T> m1 = mu8(p3, p2, p1, k);
+    const Row12<T> p4 = ld12_row(row(j0 + 2), x0, mx);
+    Row8<T> m2 = mu8(p4, p3, p2, k);
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+      // row j0 + o: phi rows (o + 1, o + 2, o + 3) of p0 .. p4, mu rows (o, o + 1, o + 2) of m0 .. m3
+      T dxp[4], dyp[4], dxm[4], dym[4];
+      if (o == 0) {
+        grad4<NEG>(mid8(p3), mid8(p2), mid8(p1), sc.w0, sc.w1, inv2h, dxp, dyp);
+        grad4<NEG>(m2, m1, m0, sc.w0, sc.w1, inv2h, dxm, dym);
+      } else {
+        const Row12<T> p5 = ld12_row(row(j0 + 3), x0, mx);
+        const Row8<T> m3 = mu8(p5, p4, p3, k);
+        grad4<NEG>(mid8(p4), mid8(p3), mid8(p2), sc.w0, sc.w1, inv2h, dxp, dyp);
+        grad4<NEG>(m3, m2, m1, sc.w0, sc.w1, inv2h, dxm, dym);
+      }
+      T r[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) r[p] = cf * diff_of_products(dxp[p], dym[p], dyp[p], dxm[p]);
+      st4(buf + o * nx + x0, r[0], r[1], r[2], r[3]);
+    }
+  }
+}
+
 // ====================================================== forward row transforms
-// Work items: one per row pair p = rows (2p, 2p+1); mode 1: g -> xs_g, plus
-// the low row modes of g (FP32, P = 16); mode 2: omega -> xs_w (the row half
-// of the transform that seeds w_hat).  Each item stages the two real rows
-// (a, b) in shared memory and transforms a + i b, so every output chunk of
-// the pair is one whole 32-byte piece.  (Stage 1's row transforms are fused
-// with its stencil: k_stage1_rows.)
+// Work items: one per row pair p = rows (2p, 2p+1).  Mode 1 is stage 2: the
+// stage-2 stencil of the pair (stage2_pair) computed straight into the
+// staging buffer, then its row transform -> xs_g, plus the low row modes of g
+// (FP32 inertial, P = 16); g itself never reaches HBM.  Mode 2: omega ->
+// xs_w (the row half of the transform that seeds w_hat), staged with
+// asynchronous copies.  Each item holds the two real rows (a, b) in shared
+// memory and transforms a + i b, so every output chunk of the pair is one
+// whole 32-byte piece.  (Stage 1's row transforms are fused with its
+// stencil: k_stage1_rows.)
 template <class T, int LN, int P, int MODE>
 __global__ void __launch_bounds__(rowfwd_cta_threads(P), rowfwd_min_ctas<T>(P)) k_rowfwd(const MemberDesc* __restrict__ descs, int log2ny,
                                                                const cplx<T>* __restrict__ tw) {
@@ -155,11 +241,13 @@ __global__ void __launch_bounds__(rowfwd_cta_threads(P), rowfwd_min_ctas<T>(P)) 
   unsigned char* base = smem_raw + (size_t)inst * rowfwd_inst_bytes(nx, sizeof(T));
   T* stage = reinterpret_cast<T*>(base);
   C* Z = reinterpret_cast<C*>(base + 2 * (size_t)nx * sizeof(T));
-  const T* src = mode == 1 ? static_cast<const T*>(D.gbuf) : static_cast<const T*>(D.omega);
+  const T* src = mode == 1 ? static_cast<const T*>(D.phi) : static_cast<const T*>(D.omega);
   C* tws = reinterpret_cast<C*>(smem_raw + (size_t)ipc * rowfwd_inst_bytes(nx, sizeof(T)));
   stage_tables_to_smem(tws, tw, log2nx, log2_points<P>(), threadIdx.x, blockDim.x);
+  const Shear<T> sc(*D.st, true);                      // stage 2: s^{n+1}
+  const int my = ny - 1;
 
-  auto issue = [&](int w) {
+  auto issue = [&](int w) {                            // mode 2: stage omega's two rows
     if (w < nitems) {
       const T* ra = src + ((size_t)(2 * w) << log2nx);
       copy_async(stage, ra, nx * (int)sizeof(T), t, Tf);
@@ -167,15 +255,27 @@ __global__ void __launch_bounds__(rowfwd_cta_threads(P), rowfwd_min_ctas<T>(P)) 
     }
     cp_async_commit();
   };
+  auto prefetch = [&](int w) {                         // mode 1: ask L2 for phi's rows 2w - 2 .. 2w + 3
+    if (w < nitems && t < 6) l2_prefetch(src + ((size_t)((2 * w - 2 + t) & my) << log2nx), (unsigned)(nx * sizeof(T)));
+  };
 
   const int iters = persistent_iters(nitems, ipc);
   int w = blockIdx.x * ipc + inst;
-  issue(w);
+  if (MODE == 1) prefetch(w);
+  else issue(w);
   for (int it = 0; it < iters; ++it, w += stride) {
     const bool active = w < nitems;
     const int p = w;
-    cp_async_wait_all();
-    __syncthreads();
+    if constexpr (MODE == 1) {
+      const int j0 = 2 * (active ? w : 0);
+      if (sc.d > 0) stage2_pair<true>(D, src, stage, j0, log2nx, my, sc, t, Tf);
+      else stage2_pair<false>(D, src, stage, j0, log2nx, my, sc, t, Tf);
+      __syncthreads();                                 // the pair's g complete
+      prefetch(w + stride);                            // the next item's rows, during the transform
+    } else {
+      cp_async_wait_all();
+      __syncthreads();
+    }
     if constexpr (sizeof(T) == 4 && P == 16 && MODE == 1) {   // the force's low row modes, part 1
       if (D.low == 1) low_row_terms<LN>(reinterpret_cast<const float*>(stage), reinterpret_cast<float*>(Z), tws, t, D);
     }
@@ -186,7 +286,7 @@ __global__ void __launch_bounds__(rowfwd_cta_threads(P), rowfwd_min_ctas<T>(P)) 
       v[q] = C{stage[i], stage[nx + i]};
     }
     __syncthreads();                                    // stage free
-    issue(w + stride);                                  // next item streams in during the transform
+    if (MODE == 2) issue(w + stride);                   // next item streams in during the transform
     if constexpr (sizeof(T) == 4 && P == 16 && MODE == 1) {
       if (D.low == 1) low_row_reduce<LN>(reinterpret_cast<float*>(Z), t, D, p, active, log2ny);
     }
@@ -594,7 +694,7 @@ void launch_row_kernel(int kind, const MemberDesc* d, int nmem, int log2nx, int 
     return;
   }
   const dim3 grid(c.grid_x, nmem);
-  const bool fwd = kind == KIND_ROWFWD_G || kind == KIND_ROWFWD_OMEGA;
+  const bool fwd = kind == KIND_STAGE2 || kind == KIND_ROWFWD_OMEGA;
   const int mode = fwd ? (kind == KIND_ROWFWD_OMEGA ? 2 : 1) : (kind == KIND_ROWINV_PHI ? 0 : 1);
   with_log2n(log2nx, [&](auto L) {
     constexpr int LN = decltype(L)::value;
@@ -617,7 +717,7 @@ int row_kernel_occupancy(int kind, int log2nx, int variant, int threads, size_t 
     });
     return nb < 1 ? 1 : nb;
   }
-  const bool fwd = kind == KIND_ROWFWD_G;
+  const bool fwd = kind == KIND_STAGE2;
   const int mode = fwd ? 1 : (kind == KIND_ROWINV_PHI ? 0 : 1);
   with_log2n(log2nx, [&](auto L) {
     constexpr int LN = decltype(L)::value;

@@ -9,6 +9,10 @@ results the paper reports, on the seeded quench.
 - Section VIII: without inertia, under shear the long domain axis L_par grows
   without bound until it spans the system, with the domains aligned along the
   flow (Eq. L_matrix's principal axes).
+- Section VIII: with inertia (run R020 of Table Ic, in the paper's units) L_par
+  and L_perp saturate, fluctuating about constant means well below the system
+  size, while without inertia (DV4 of Table Id) L_par keeps growing to the
+  system size.
 """
 import math
 
@@ -122,3 +126,44 @@ def test_configs_and_logged_run(tmp_path):
     ens = configs.make("c4_ensemble_fp32")
     assert len(ens.members) == 96
     ens.close()
+
+
+def _lengths_vs_strain(name, nx, ny, strains, prec=shf.SHF_FP32):
+    """L_par, L_perp (Eq. L_matrix) of Table I set ``name`` in the paper's units
+    (dx = 1/512, kappa = M = l^2) on nx x ny, at the given strains, from the
+    seeded +-0.01 quench."""
+    from paper_0710_5912_gb300 import configs
+    _, _, dx, p = configs.paper_units(name)
+    out = []
+    with shf.Grid(nx, ny, dx, prec) as g:
+        g.set_params(**p)
+        g.init_noise(0, 0.01)
+        n = 0
+        for st in strains:
+            target = int(round(st / (p["gdot"] * p["dt"])))
+            g.step(target - n)
+            n = target
+            _, (Lpar, Lperp) = g.gradient_tensor()
+            out.append((Lpar, Lperp))
+    return np.array(out)
+
+
+def test_sheared_domains_saturate_with_inertia_and_span_the_box_without():
+    """Section VIII's central contrast, at Table I parameters (paper units).
+    R020s (Table Ic: rho = 16180, eta = 0.0785, gdot = 0.0256, 1024 x 512,
+    Lambda_x = 2): after 30 strain units L_par and L_perp fluctuate about
+    constant means (the means over strains 30-60 and 65-100 agree within 25%)
+    with L_par below Lambda_x / 3.  DV4s (Table Id: rho = 0, eta = 1,
+    gdot = 0.01) on a 512 x 256 box at the same mesh (Lambda_x = 1): L_par
+    grows more than threefold between strains 10 and 60 and exceeds half the
+    box."""
+    strains = np.arange(30.0, 101.0, 5.0)
+    L = _lengths_vs_strain("R020s", 1024, 512, strains)
+    early, late = L[strains <= 60], L[strains > 60]
+    for k, what in ((0, "L_par"), (1, "L_perp")):
+        ratio = late[:, k].mean() / early[:, k].mean()
+        assert 0.75 < ratio < 1.25, (what, ratio, L[:, k])
+    assert L[:, 0].max() < 2.0 / 3.0, L[:, 0]
+    D = _lengths_vs_strain("DV4s", 512, 256, [10.0, 60.0])
+    assert D[1, 0] > 3.0 * D[0, 0], D
+    assert D[1, 0] > 0.5, D
