@@ -238,8 +238,9 @@ int shf_noise_fill(double* out, int64_t count, uint64_t seed, double amp);
  *     call synchronises it before returning.
  *   mean_phi: receives the mean; set to NaN first, so it holds NaN after any
  *     error.
- * Same reductions as shf_mass (1024-CTA Neumaier partials folded in CTA
- * order), so for the same field both return the same bits.  Allocates
+ * Same reductions as shf_mass (per-CTA Neumaier partials over the same CTAs,
+ * at most 1024, folded in CTA order), so for the same field both return the
+ * same bits.  Allocates
  * nothing: the partials live in a fixed 24,600-byte device array of the
  * library, which every device that loads the library holds until the process
  * exits.  The first call on a device looks up that array's device address

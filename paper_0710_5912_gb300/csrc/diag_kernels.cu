@@ -120,7 +120,7 @@ __device__ __forceinline__ float mass_group(const float4 (&v)[kMassVec], float& 
 __global__ void __launch_bounds__(256) k_mass_partials_f32(const float* __restrict__ f, long long count,
                                                            double* __restrict__ out) {
   __shared__ double sh[2 * 2 * 32];
-  double acc = 0.0;
+  double acc4[4] = {0.0, 0.0, 0.0, 0.0};                // groups g go to acc4[g mod 4]: short FP64 chains
   float tail = 0.f;
   unsigned bad = 0;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -128,12 +128,20 @@ __global__ void __launch_bounds__(256) k_mass_partials_f32(const float* __restri
   const long long n4 = (reinterpret_cast<uintptr_t>(f) & 15) == 0 ? count / 4 : 0;
   const float4* f4 = reinterpret_cast<const float4*>(f);
   long long e = tid;
-  for (; e + (kMassVec - 1) * stride < n4; e += kMassVec * stride) {
+  int g = 0;
+  for (; e + (kMassVec - 1) * stride < n4; e += kMassVec * stride, ++g) {
     float4 v[kMassVec];
 #pragma unroll
     for (int k = 0; k < kMassVec; ++k) v[k] = __ldcs(f4 + e + k * stride);
-    acc += (double)mass_group(v, tail, bad);
+    const double h = (double)mass_group(v, tail, bad);
+    switch (g & 3) {
+      case 0: acc4[0] += h; break;
+      case 1: acc4[1] += h; break;
+      case 2: acc4[2] += h; break;
+      default: acc4[3] += h; break;
+    }
   }
+  double acc = (acc4[0] + acc4[1]) + (acc4[2] + acc4[3]);
   for (; e < n4; e += stride) {                        // the last partial group
     const float4 a = __ldcs(f4 + e);
     bad |= nonfinite_bit(a.x) | nonfinite_bit(a.y) | nonfinite_bit(a.z) | nonfinite_bit(a.w);
@@ -148,12 +156,45 @@ __global__ void __launch_bounds__(256) k_mass_partials_f32(const float* __restri
     bad |= nonfinite_bit(v);
     acc += (double)v;
   }
-  double s[2] = {acc, bad ? 1.0 : 0.0}, c[2] = {(double)tail, 0.0};
-  block_reduce_pairs<2>(s, c, sh);
-  if (threadIdx.x == 0) {
-    out[3 * blockIdx.x + 0] = s[0];
-    out[3 * blockIdx.x + 1] = c[0];
-    out[3 * blockIdx.x + 2] = s[1] + c[1];
+  // the CTA's sum: Neumaier over the lanes (fixed tree), then over the warps
+  // in order; the non-finite flags by an integer OR (no FP64 work for them)
+  double s = acc, c = (double)tail;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double os = __shfl_down_sync(0xffffffffu, s, off), oc = __shfl_down_sync(0xffffffffu, c, off);
+    if (lane < off) {
+      neumaier_add(s, c, os);
+      c += oc;
+    }
+  }
+  bad = __reduce_or_sync(0xffffffffu, bad);
+  __shared__ unsigned shbad[32];
+  if (lane == 0) {
+    sh[warp] = s;
+    sh[32 + warp] = c;
+    shbad[warp] = bad;
+  }
+  __syncthreads();
+  if (warp == 0) {                                     // the warps' sums in a fixed pairwise tree
+    const int nw = (blockDim.x + 31) >> 5;
+    s = lane < nw ? sh[lane] : 0.0;
+    c = lane < nw ? sh[32 + lane] : 0.0;
+    unsigned b = lane < nw ? shbad[lane] : 0u;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const double os = __shfl_down_sync(0xffffffffu, s, off), oc = __shfl_down_sync(0xffffffffu, c, off);
+      if (lane < off) {
+        neumaier_add(s, c, os);
+        c += oc;
+      }
+    }
+    b = __reduce_or_sync(0xffffffffu, b);
+    if (lane == 0) {
+      out[3 * blockIdx.x + 0] = s;
+      out[3 * blockIdx.x + 1] = c;
+      out[3 * blockIdx.x + 2] = b ? 1.0 : 0.0;
+    }
   }
 }
 
@@ -181,11 +222,10 @@ __global__ void __launch_bounds__(256) k_mass_partials(const T* __restrict__ f, 
 // Fold of the per-CTA mass partials into out[0..2] = (sum, compensation,
 // non-finite count), in a fixed two-level order: lane l of one warp folds
 // partials [l G, (l + 1) G) in order (G = ceil(ctas / 32)) with Neumaier's
-// steps, then lane 0 folds the 32 lane results in lane order.  Every caller
+// steps, then the 32 lane results meet in a fixed pairwise tree.  Every caller
 // (shf_mass, shf_sync, shf_mass_static) uses this one fold, so they agree
 // bit for bit on the same field.
 __global__ void k_mass_fold(const double* __restrict__ part, int ctas, double* __restrict__ out) {
-  __shared__ double sh[3 * 32];
   const int lane = threadIdx.x;
   const int G = (ctas + 31) / 32;
   double s = 0.0, c = 0.0, nf = 0.0;
@@ -194,20 +234,21 @@ __global__ void k_mass_fold(const double* __restrict__ part, int ctas, double* _
     c += part[3 * b + 1];
     nf += part[3 * b + 2];
   }
-  sh[lane] = s;
-  sh[32 + lane] = c;
-  sh[64 + lane] = nf;
-  __syncwarp();
-  if (lane == 0) {
-    double S = 0.0, C = 0.0, NF = 0.0;
-    for (int l = 0; l < 32; ++l) {
-      neumaier_add(S, C, sh[l]);
-      C += sh[32 + l];
-      NF += sh[64 + l];
+  // the 32 lane results in a fixed pairwise tree (short FP64 dependency chains)
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double os = __shfl_down_sync(0xffffffffu, s, off), oc = __shfl_down_sync(0xffffffffu, c, off);
+    const double on = __shfl_down_sync(0xffffffffu, nf, off);
+    if (lane < off) {
+      neumaier_add(s, c, os);
+      c += oc;
+      nf += on;
     }
-    out[0] = S;
-    out[1] = C;
-    out[2] = NF;
+  }
+  if (lane == 0) {
+    out[0] = s;
+    out[1] = c;
+    out[2] = nf;
   }
 }
 
@@ -347,7 +388,10 @@ void launch_convert_out(const T* src, double* dst, long long count, cudaStream_t
 template <class T>
 int launch_mass_partials(const T* f, long long count, double* out, int max_ctas, cudaStream_t st) {
   const int thr = 256;
-  long long ctas = (count + thr - 1) / thr;
+  // FP32: at least 256 values per thread, so that few threads take part in the
+  // FP64 reductions (this part's FP64 pipe is narrow); FP64: one per thread
+  const long long per = sizeof(T) == 4 ? 256 : 1;
+  long long ctas = (count + thr * per - 1) / (thr * per);
   if (ctas > max_ctas) ctas = max_ctas;
   if (ctas < 1) ctas = 1;
   if constexpr (sizeof(T) == 4) k_mass_partials_f32<<<(int)ctas, thr, 0, st>>>(f, count, out);
