@@ -488,7 +488,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, **PARAMS, "seed": SEED, "amp": AMP,
                            "parallelism": f"replicas x{world}" if world > 1 else "single grid",
-                           "l2": "state + scratch 576 MiB > L2 (129 MB): inputs larger than L2, no flush",
+                           "l2": "state + scratch ~640 MiB > L2 (129 MB): inputs larger than L2, no flush",
                            "autotuned": {"stage1_points": tuned[0][0], "stage2_points": tuned[0][1]}},
                 "roofline": roofline, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e,
                 # the step kernels, each launched once per step (omega_hat is seeded during the warm-up)
