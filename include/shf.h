@@ -148,7 +148,10 @@ int shf_step(shf_grid* g, int64_t nsteps);
  * production runs. */
 int shf_profile_step(shf_grid* g, int64_t nsteps, double* kernel_ms, int nkinds);
 
-/* Wait for queued work; returns SHF_ENONFINITE if phi holds NaN/Inf. */
+/* Wait for queued work; returns SHF_ENONFINITE if phi holds NaN/Inf, and
+ * SHF_ETIMEOUT if a kernel's bounded wait for its own asynchronous (TMA)
+ * input copies gave up since the last check (the kernel then stopped early;
+ * the state is not a valid step; the flag is cleared). */
 int shf_sync(shf_grid* g);
 
 /* Copy the state to host arrays (ny*nx doubles each; any may be NULL).

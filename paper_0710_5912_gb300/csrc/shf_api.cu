@@ -7,8 +7,11 @@
 #include <cstddef>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
+
+#include <cuda.h>   // CUtensorMap and its enums (the encoder is fetched at run time)
 
 #include "../../include/shf.h"
 #include "shf_internal.cuh"
@@ -38,6 +41,7 @@ struct Member {
   void* w_hat = nullptr;      // FP32: omega's 2D transform (inertial), see MemberDesc
   void* low_rows = nullptr;   // FP32: low row modes of g
   void* low_hat = nullptr;    // FP32: low 2D modes of g
+  void* tmap = nullptr;       // FP32, nx >= 1024: TMA tensor maps of xs_phi, xs_g, xs_w (see MemberDesc)
   StepState* d_st = nullptr;  // into the owner's step-state array
   int cls = -1, slot = -1;
 };
@@ -51,6 +55,41 @@ struct SizeClass {
   RowCfg sfrows{};
   ColCfg sfcols{};
 };
+
+// cuTensorMapEncodeTiled from the driver, fetched once at run time (the
+// library links the runtime only); null if the driver does not provide it
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+// An FP32 x-spectral buffer (element (j, m) at ((m >> 1) ny + j) 2 + (m & 1)
+// complex) as a 3D tensor of floats: d0 = the 4 floats of a row's two-mode
+// chunk (16 bytes), d1 = the row j (stride 16 bytes), d2 = the chunk column
+// (stride 16 ny bytes).  Boxes of {4, 2, 256} are one row pair's 32-byte
+// pieces of 256 chunk columns; no L2 promotion (the pieces lie 16 ny bytes
+// apart).
+bool encode_xs_map(CUtensorMap* out, void* base, int nx, int ny) {
+  const EncodeTiledFn fn = encode_tiled_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {4, (cuuint64_t)ny, (cuuint64_t)(nx / 4)};
+  const cuuint64_t strides[2] = {16, (cuuint64_t)ny * 16};
+  const cuuint32_t box[3] = {4, 2, 256};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return fn(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
 
 int ilog2(int v) {
   int l = 0;
@@ -73,6 +112,7 @@ struct shf_grid {
   std::vector<Member> members;
   std::vector<SizeClass> classes;
   StepState* d_state = nullptr;   // per member: counter and strain of the current step
+  int* d_err = nullptr;           // set by a kernel whose bounded wait gave up (SHF_ETIMEOUT)
   long long n = 0;
   void* d_tw = nullptr;     // W[k] = exp(2 pi i k / NMAX) (shared-memory FFTs of the diagnostics)
   void* d_twff = nullptr;   // FP32 grids: W[k] as float pairs (hi, lo) per component, float4 per k
@@ -176,7 +216,8 @@ int sm_count() {
 // CTA size; the grid holds as many CTAs as are resident at once (occupancy
 // query), shared over the members of the launch.
 template <class T>
-LaunchCfg persistent_cfg(int kind, int nfft, int max_inst, int items, size_t inst_bytes, int nmem, int P = kP) {
+LaunchCfg persistent_cfg(int kind, int nfft, int max_inst, int items, size_t inst_bytes, int nmem, int P = kP,
+                         size_t extra = 0) {
   LaunchCfg c{};
   const bool fwd = kind == KIND_STAGE1 || kind == KIND_STAGE2;
   const bool rows = fwd || kind == KIND_ROWINV_PHI || kind == KIND_ROWINV_FLOW;
@@ -188,10 +229,10 @@ LaunchCfg persistent_cfg(int kind, int nfft, int max_inst, int items, size_t ins
   int ipc = cta / Tf;
   if (ipc < 1) ipc = 1;
   if (ipc > max_inst) ipc = max_inst;
-  while (ipc > 1 && ipc * inst_bytes + tab > kSmemLimit) ipc /= 2;
+  while (ipc > 1 && ipc * inst_bytes + tab + extra > kSmemLimit) ipc /= 2;
   c.inst_per_cta = ipc;
   c.threads = ipc * Tf;
-  c.smem = ipc * inst_bytes + tab;
+  c.smem = ipc * inst_bytes + tab + extra;
   c.variant = rows ? P : 0;
   const int work = (items + ipc - 1) / ipc;
   const int resident = step_kernel_occupancy<T>(kind, log2n, c.variant, c.threads, c.smem) * sm_count();
@@ -248,8 +289,10 @@ void configure_class_t(SizeClass& cl, Tune tune) {
   }
   cl.cfg[KIND_COLPASS_FLOW] = cl.cfg[KIND_COLPASS_PHI];
   const int PI = rowinv_default_points<T>();
-  cl.cfg[KIND_ROWINV_PHI] = persistent_cfg<T>(KIND_ROWINV_PHI, nx, ny / 2, ny / 2, rowinv_inst_bytes(nx, R), nmem, PI);
-  cl.cfg[KIND_ROWINV_FLOW] = persistent_cfg<T>(KIND_ROWINV_FLOW, nx, ny / 2, ny, rowinv_inst_bytes(nx, R), nmem, PI);
+  cl.cfg[KIND_ROWINV_PHI] = persistent_cfg<T>(KIND_ROWINV_PHI, nx, ny / 2, ny / 2, rowinv_inst_bytes(nx, R), nmem, PI,
+                                              kRowinvBarBytes);
+  cl.cfg[KIND_ROWINV_FLOW] = persistent_cfg<T>(KIND_ROWINV_FLOW, nx, ny / 2, ny, rowinv_inst_bytes(nx, R), nmem, PI,
+                                               kRowinvBarBytes);
   cl.sfrows = sf_row_cfg(nx, ny, nx * Cx);
   cl.sfcols = sf_col_cfg(nx, ny, Cx + 12, Cx);
 }
@@ -303,6 +346,8 @@ MemberDesc make_desc(const shf_grid* o, const Member& m) {
   d.w_hat = m.w_hat;
   d.low_rows = m.low_rows;
   d.low_hat = m.low_hat;
+  d.tmap = m.tmap;
+  d.err = o->d_err;
   d.wspec = fp32 && !d.stokes ? 1 : 0;
   d.low = fp32 ? (m.rho > 0.0 ? 1 : 2) : 0;   // 2: Stokes, F's low row modes formed exactly
   const int lowm_max = d.low == 2 ? kLowMExact : kLowM;
@@ -384,9 +429,11 @@ void free_all(shf_grid* g) {
     cudaFree(m.w_hat);
     cudaFree(m.low_rows);
     cudaFree(m.low_hat);
+    cudaFree(m.tmap);
   }
   for (auto& cl : g->classes) cudaFree(cl.d_desc);
   cudaFree(g->d_state);
+  cudaFree(g->d_err);
   cudaFree(g->d_tw);
   cudaFree(g->d_twff);
   cudaFree(g->d_twr);
@@ -439,6 +486,8 @@ int build(shf_grid* g, const std::vector<int>& nx, const std::vector<int>& ny, c
   if (cudaMalloc(&g->d_state, nm * sizeof(StepState)) != cudaSuccess)
     return fail(g, SHF_ENOMEM, "counter allocation failed");
   SHF_CUDA(g, cudaMemsetAsync(g->d_state, 0, nm * sizeof(StepState), g->stream));
+  if (cudaMalloc(&g->d_err, sizeof(int)) != cudaSuccess) return fail(g, SHF_ENOMEM, "flag allocation failed");
+  SHF_CUDA(g, cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream));
   const size_t R = real_size(g);
   for (int r = 0; r < nm; ++r) {
     Member& m = g->members[r];
@@ -468,6 +517,14 @@ int build(shf_grid* g, const std::vector<int>& nx, const std::vector<int>& ny, c
       SHF_CUDA(g, cudaMemsetAsync(m.w_hat, 0, bytes, g->stream));
       SHF_CUDA(g, cudaMemsetAsync(m.low_rows, 0, lr, g->stream));
       SHF_CUDA(g, cudaMemsetAsync(m.low_hat, 0, lh, g->stream));
+      if (m.nx >= 1024) {                               // TMA maps for the inverse row passes
+        CUtensorMap maps[3];
+        if (encode_xs_map(&maps[0], m.xs[0], m.nx, m.ny) && encode_xs_map(&maps[1], m.xs[3], m.nx, m.ny) &&
+            encode_xs_map(&maps[2], m.xs[2], m.nx, m.ny)) {
+          if (cudaMalloc(&m.tmap, sizeof(maps)) != cudaSuccess) return fail(g, SHF_ENOMEM, "tensor map allocation failed");
+          SHF_CUDA(g, cudaMemcpy(m.tmap, maps, sizeof(maps), cudaMemcpyHostToDevice));
+        }
+      }
     }
     int found = -1;
     for (size_t c = 0; c < g->classes.size(); ++c)
@@ -1314,6 +1371,12 @@ int shf_sync(shf_grid* g) {
   SHF_CUDA(g, cudaSetDevice(o->device));
   SHF_CUDA(g, cudaStreamSynchronize(o->stream));
   SHF_CUDA(g, cudaGetLastError());
+  int err = 0;
+  SHF_CUDA(g, cudaMemcpy(&err, o->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (err) {
+    SHF_CUDA(g, cudaMemset(o->d_err, 0, sizeof(int)));
+    return fail(g, SHF_ETIMEOUT, "a kernel's bounded wait for its input copies gave up");
+  }
   std::vector<int> which;
   if (g->kind == 1) {
     for (size_t r = 0; r < o->members.size(); ++r) which.push_back((int)r);

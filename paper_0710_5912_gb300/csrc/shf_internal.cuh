@@ -45,6 +45,12 @@ struct MemberDesc {
   void* w_hat;
   void* low_rows;
   void* low_hat;
+  // FP32 members with rows of 1024 points or more: TMA tensor maps (CUtensorMap,
+  // 128 bytes each, in device memory) of xs_phi, xs_g and xs_w, each viewed as
+  // [nx / 4 chunk columns][ny rows][4 floats], for the inverse row passes'
+  // row-pair gathers; null: those gathers use per-thread asynchronous copies
+  const void* tmap;
+  int* err;       // device flag of the grid: a bounded wait in a kernel gave up (SHF_ETIMEOUT)
   StepState* st;  // device step counter and strain of the current step
   // parameters and derived constants (double; cast to the working precision)
   double a, b, kappa, M, eta, rho, gdot, dt, dx;
@@ -124,6 +130,9 @@ __host__ __device__ constexpr size_t colchunk_cta_bytes(int ny) {
 __host__ __device__ constexpr size_t stage1_inst_bytes(int nx, size_t real_bytes) {
   return round128((size_t)padded_len(nx) * 2 * real_bytes);
 }
+// the inverse row pass's mbarriers (one per instance, at most 4 with TMA),
+// after its twiddle table
+constexpr size_t kRowinvBarBytes = 128;
 __host__ __device__ constexpr size_t rowinv_inst_bytes(int nx, size_t real_bytes) {
   return round128(((size_t)nx + (size_t)padded_len(nx)) * 2 * real_bytes);
 }

@@ -549,15 +549,46 @@ __global__ void __launch_bounds__(rowfwd_cta_threads(P), P == 16 ? 2 : min_ctas<
   C* tws = reinterpret_cast<C*>(smem_raw + (size_t)ipc * rowinv_inst_bytes(nx, sizeof(T)));
   stage_tables_to_smem(tws, tw, log2nx, log2_points<P>(), threadIdx.x, blockDim.x);
 
+  // FP32 rows of >= 1024 points with tensor maps: one thread per instance loads
+  // the item's row pair with TMA boxes of {4 floats, 2 rows, 256 chunks} (the
+  // staged layout is then [chunk][row][16 bytes]); else every thread gathers
+  // its chunks with 16-byte asynchronous copies ([row][chunk][16 bytes])
+  constexpr int kBox = 256;
+  const bool tma = sizeof(T) == 4 && P == 16 && D.tmap != nullptr && nchunk % kBox == 0 &&
+                   (smem_addr(smem_raw) & 127u) == 0;   // uniform; TMA destinations 128-byte aligned
+  // the instances' mbarriers sit after the twiddle table (kRowinvBarBytes of
+  // the launch's dynamic shared memory), so that no static shared memory
+  // shifts the 128-byte alignment of the staging buffers the TMA writes
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(
+      smem_raw + (size_t)ipc * rowinv_inst_bytes(nx, sizeof(T)) + stage_table_bytes(log2nx, log2_points<P>(), sizeof(T)));
+  unsigned long long* bar = bars + (inst & 3);
+  unsigned phase = 0;
+  const char* tmaps = static_cast<const char*>(D.tmap);
+  if (tma && t == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+    for (int k = 0; k < 3; ++k) tmap_acquire(tmaps + 128 * k);
+  }
+  __syncthreads();
+
   auto issue = [&](int w) {
     if (w < nitems) {
       const int sub = w % nsub;
-      const C* src = static_cast<const C*>(mode == 0 ? D.xs_phi : (sub == 0 ? D.xs_g : D.xs_w));
       const int j0 = 2 * (w / nsub);
-      for (int cb = t; cb < nchunk; cb += Tf) {
-        const C* g = src + ((((size_t)cb * ny) + j0) << LC);
-        cp_async16(stage + CL * cb, g);
-        cp_async16(stage + CL * (nchunk + cb), g + H);
+      if (tma) {
+        if (t == 0) {
+          const char* tm = tmaps + 128 * (mode == 0 ? 0 : (sub == 0 ? 1 : 2));
+          fence_proxy_async_smem();                     // the stage's earlier reads come first
+          mbar_arrive_expect_tx(bar, (unsigned)(2 * nchunk * 16));
+          for (int k = 0; k < nchunk / kBox; ++k) tma_load_3d(stage + 2 * CL * kBox * k, tm, 0, j0, kBox * k, bar);
+        }
+      } else {
+        const C* src = static_cast<const C*>(mode == 0 ? D.xs_phi : (sub == 0 ? D.xs_g : D.xs_w));
+        for (int cb = t; cb < nchunk; cb += Tf) {
+          const C* g = src + ((((size_t)cb * ny) + j0) << LC);
+          cp_async16(stage + CL * cb, g);
+          cp_async16(stage + CL * (nchunk + cb), g + H);
+        }
       }
       // the item's increment bases, read after its transform: into L2 now
       const bool base = mode == 0 || (sub == 1 && !D.wspec);
@@ -586,12 +617,23 @@ __global__ void __launch_bounds__(rowfwd_cta_threads(P), P == 16 ? 2 : min_ctas<
       const T* nq = static_cast<const T*>(kind == 0 ? D.nyq_phi : D.nyq_omega);
       zn = C{-nq[j0] * rn, -nq[j1] * rn};
     }
-    cp_async_wait_all();
-    __syncthreads();
+    bool ok = true;
+    if (tma) {
+      if (active) {
+        ok = mbar_wait_bounded(bar, phase);
+        phase ^= 1u;
+      }
+    } else {
+      cp_async_wait_all();
+    }
+    if (!__syncthreads_and(ok)) {                       // the item's copies never arrived: flag it and stop
+      if (threadIdx.x == 0) atomicOr(D.err, 1);
+      return;
+    }
     for (int cb = t; cb < nchunk; cb += Tf) {
       C Av[CL], Bv[CL];
-      load16(stage + CL * cb, Av);
-      load16(stage + CL * (nchunk + cb), Bv);
+      load16(stage + (tma ? 2 * CL * cb : CL * cb), Av);
+      load16(stage + (tma ? 2 * CL * cb + CL : CL * (nchunk + cb)), Bv);
 #pragma unroll
       for (int c = 0; c < CL; ++c) {
         const int k = (cb << LC) + c;
