@@ -279,7 +279,7 @@ void configure_class_t(SizeClass& cl, Tune tune) {
     LaunchCfg c{};
     c.inst_per_cta = 1;
     c.threads = 2 * (ny / 16);
-    c.smem = colchunk_cta_bytes(ny) + stage_table_bytes(cl.log2ny, 4, R);
+    c.smem = colchunk_cta_bytes(ny) + stage_table_bytes(cl.log2ny, 4, R) + kColBarBytes;
     const int resident = step_kernel_occupancy<T>(KIND_COLPASS_PHI, cl.log2ny, 0, c.threads, c.smem) * sm_count();
     int g = (resident + nmem - 1) / nmem;
     if (g > nx / 4) g = nx / 4;

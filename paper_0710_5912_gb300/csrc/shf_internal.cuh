@@ -120,7 +120,9 @@ __host__ __device__ constexpr size_t colsingle_inst_bytes(int ny) {
   return round128((2 * (size_t)ny + (size_t)padded_len(ny)) * 8);
 }
 // the FP32 chunk column pass (ny >= 512): one CTA stages a two-mode chunk of
-// two fields (16-byte rows) and holds one padded exchange buffer per mode
+// two fields (16-byte rows) and holds one padded exchange buffer per mode;
+// its mbarrier follows the twiddle table (kColBarBytes)
+constexpr size_t kColBarBytes = 128;
 __host__ __device__ constexpr size_t colchunk_cta_bytes(int ny) {
   return round128(2 * (size_t)ny * 16 + 2 * (size_t)padded_len(ny) * 8);
 }

@@ -483,13 +483,24 @@ __device__ __forceinline__ void colpass_chunk_body(const MemberDesc& D, int log2
     __syncthreads();                                   // ost is the exchange buffers again
   };
 
+  // each field's chunk is one contiguous run of ny 16-byte rows: one thread
+  // stages it with a bulk copy completed on the CTA's mbarrier (after the
+  // twiddle table, kColBarBytes of the launch's dynamic shared memory)
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + colchunk_cta_bytes(ny) +
+                                                                  stage_table_bytes(log2ny, 4, sizeof(float)));
+  unsigned phase = 0;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
   auto issue = [&](int cb) {
-    if (cb < nitems) {
-      copy_async(st0, reinterpret_cast<const float4*>(in0) + (size_t)cb * ny, ny * 16, threadIdx.x, blockDim.x);
-      if (two)
-        copy_async(st1, reinterpret_cast<const float4*>(in1) + (size_t)cb * ny, ny * 16, threadIdx.x, blockDim.x);
+    if (cb < nitems && threadIdx.x == 0) {
+      fence_proxy_async_smem();                         // the stage's earlier reads come first
+      mbar_arrive_expect_tx(bar, (two ? 2u : 1u) * ny * 16u);
+      bulk_g2s(st0, reinterpret_cast<const float4*>(in0) + (size_t)cb * ny, ny * 16u, bar);
+      if (two) bulk_g2s(st1, reinterpret_cast<const float4*>(in1) + (size_t)cb * ny, ny * 16u, bar);
     }
-    cp_async_commit();
   };
 
   const ColConsts<T> K(D, KIND == 0 ? 0 : 1, ny);
@@ -498,8 +509,15 @@ __device__ __forceinline__ void colpass_chunk_body(const MemberDesc& D, int log2
   issue(cb);
   for (int it = 0; it < iters; ++it, cb += stride) {
     const bool active = cb < nitems;
-    cp_async_wait_all();
-    __syncthreads();
+    bool ok = true;
+    if (active) {
+      ok = mbar_wait_bounded(bar, phase);
+      phase ^= 1u;
+    }
+    if (!__syncthreads_and(ok)) {                       // the chunk never arrived: flag it and stop
+      if (threadIdx.x == 0) atomicOr(D.err, 1);
+      return;
+    }
     C a[P], b[P];                                       // mode 2 cb + sub of the two fields
 #pragma unroll
     for (int q = 0; q < P; ++q) {
