@@ -125,6 +125,9 @@ struct shf_grid {
   size_t pinned_count = 0;
   cudaGraphExec_t graph = nullptr;
   cudaStream_t io_stream = nullptr;   // shf_step_host_f32: the early phi download
+  std::vector<cudaStream_t> class_streams;   // ensembles: one stream per size class
+  cudaEvent_t fork = nullptr;                // ensembles: class streams wait on it
+  std::vector<cudaEvent_t> joins;            // ensembles: the grid's stream waits on them
   cudaEvent_t phi_done = nullptr;     // recorded after the last step's phi row inverse
   bool what_valid = false;            // FP32: w_hat holds the 2D transform of the current omega
   std::vector<shf_grid*> views;
@@ -442,6 +445,9 @@ void free_all(shf_grid* g) {
   if (g->h_pinned) cudaFreeHost(g->h_pinned);
   if (g->phi_done) cudaEventDestroy(g->phi_done);
   if (g->io_stream) cudaStreamDestroy(g->io_stream);
+  for (auto st : g->class_streams) cudaStreamDestroy(st);
+  for (auto ev : g->joins) cudaEventDestroy(ev);
+  if (g->fork) cudaEventDestroy(g->fork);
   if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
   for (auto* v : g->views) delete v;
   delete g;
@@ -548,6 +554,17 @@ int build(shf_grid* g, const std::vector<int>& nx, const std::vector<int>& ny, c
     if (cudaMalloc(&cl.d_desc, cl.members.size() * sizeof(MemberDesc)) != cudaSuccess)
       return fail(g, SHF_ENOMEM, "descriptor allocation failed");
   }
+  if (g->classes.size() > 1) {                          // a stream per size class (enqueue_steps)
+    SHF_CUDA(g, cudaEventCreateWithFlags(&g->fork, cudaEventDisableTiming));
+    for (size_t c = 0; c < g->classes.size(); ++c) {
+      cudaStream_t st = nullptr;
+      cudaEvent_t ev = nullptr;
+      SHF_CUDA(g, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+      g->class_streams.push_back(st);
+      SHF_CUDA(g, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      g->joins.push_back(ev);
+    }
+  }
   for (int r = 0; r < nm; ++r) {
     int rc = upload_desc(g, r);
     if (rc) return rc;
@@ -604,15 +621,15 @@ int build(shf_grid* g, const std::vector<int>& nx, const std::vector<int>& ny, c
 
 // The launches of one step for one size class, in order (kind 0..KIND_COUNT-1).
 template <class T>
-void launch_kind(shf_grid* o, SizeClass& cl, int kind) {
+void launch_kind(shf_grid* o, SizeClass& cl, int kind, cudaStream_t st) {
   const cplx<T>* tw = static_cast<const cplx<T>*>(o->d_twr);
   if (kind == KIND_LOWMODE) {                           // FP32 only: the force's low 2D modes
     if (sizeof(T) == 4) {
       bool stokes = false;
       for (int r : cl.members) stokes = stokes || o->members[r].rho == 0.0;
       const float4* twff = static_cast<const float4*>(o->d_twff);
-      if (stokes) launch_lowrows_exact(cl.d_desc, (int)cl.members.size(), cl.log2nx, cl.log2ny, twff, o->stream);
-      launch_lowmode_cols(cl.d_desc, (int)cl.members.size(), cl.log2ny, twff, o->stream);
+      if (stokes) launch_lowrows_exact(cl.d_desc, (int)cl.members.size(), cl.log2nx, cl.log2ny, twff, st);
+      launch_lowmode_cols(cl.d_desc, (int)cl.members.size(), cl.log2ny, twff, st);
     }
     return;
   }
@@ -622,7 +639,11 @@ void launch_kind(shf_grid* o, SizeClass& cl, int kind) {
     for (int r : cl.members) (o->members[r].rho > 0.0 ? inertial : stokes) = true;
     c.variant = inertial && stokes ? 3 : (stokes ? 2 : 1);
   }
-  launch_step_kernel<T>(kind, cl.d_desc, (int)cl.members.size(), cl.log2nx, cl.log2ny, tw, c, o->stream);
+  launch_step_kernel<T>(kind, cl.d_desc, (int)cl.members.size(), cl.log2nx, cl.log2ny, tw, c, st);
+}
+template <class T>
+void launch_kind(shf_grid* o, SizeClass& cl, int kind) {
+  launch_kind<T>(o, cl, kind, o->stream);
 }
 
 constexpr int kKinds = KIND_COUNT;
@@ -652,7 +673,29 @@ void enqueue_state_init(shf_grid* o) {
   }
 }
 
+// k steps.  With several size classes (an ensemble) the classes are
+// independent runs: each advances on a stream of its own, forked from and
+// joined back to the grid's stream by events, so that the launches of small
+// classes fill the SMs the large ones leave idle (inside a graph capture these
+// become parallel branches).
+template <class T>
+void enqueue_class_steps(shf_grid* o, SizeClass& cl, long long k, cudaStream_t st) {
+  for (long long i = 0; i < k; ++i)
+    for (int kind = 0; kind < kKinds; ++kind) launch_kind<T>(o, cl, kind, st);
+}
 void enqueue_steps(shf_grid* o, long long k) {
+  if (k <= 0) return;
+  if (o->class_streams.size() == o->classes.size() && o->classes.size() > 1) {
+    cudaEventRecord(o->fork, o->stream);
+    for (size_t c = 0; c < o->classes.size(); ++c) {
+      cudaStreamWaitEvent(o->class_streams[c], o->fork, 0);
+      if (o->precision == SHF_FP64) enqueue_class_steps<double>(o, o->classes[c], k, o->class_streams[c]);
+      else enqueue_class_steps<float>(o, o->classes[c], k, o->class_streams[c]);
+      cudaEventRecord(o->joins[c], o->class_streams[c]);
+      cudaStreamWaitEvent(o->stream, o->joins[c], 0);
+    }
+    return;
+  }
   for (long long i = 0; i < k; ++i) {
     if (o->precision == SHF_FP64) enqueue_step<double>(o);
     else enqueue_step<float>(o);
