@@ -244,10 +244,11 @@ __device__ __forceinline__ void ff_mul(float a, float bh, float bl, float& ph, f
 // and the four real sums (Re r cos, Im r sin, Im r cos, Re r sin) are
 // double-float sums (TwoSum), so the result carries essentially only the
 // rounding of the coefficients themselves.  A CTA holds one output; its
-// eight warps share the rows in eighths (lanes coalesced along j, four rows in
-// flight per lane); lanes and warps are folded in a fixed order, as float
-// pairs.
+// eight warps share the rows in eighths (lanes coalesced along j, up to 16
+// rows' loads in flight per lane); lanes and warps are folded in a fixed
+// order, as float pairs.
 constexpr int kLowColsWarps = 8;
+constexpr int kLowColsRows = 512;   // rows a warp takes per round (ny = 4096: one round)
 __global__ void __launch_bounds__(kLowColsWarps * 32) k_lowmode_cols(const MemberDesc* __restrict__ descs,
                                                                      int log2ny, const float4* __restrict__ twff) {
   const MemberDesc& D = descs[blockIdx.y];
@@ -266,11 +267,12 @@ __global__ void __launch_bounds__(kLowColsWarps * 32) k_lowmode_cols(const Membe
   // low parts of the coefficients (low == 2: exact Stokes rows), else none
   const float2* lrl = D.low == 2 ? lr + ((size_t)(kLowM + 1) << log2ny) : nullptr;
   float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int jb = j0; jb < j1; jb += 128) {
-    float2 r[4], rl[4];
-    float4 w[4];
+  constexpr int U = kLowColsRows / 32;                 // rows per lane per round, all loads in flight at once
+  for (int jb = j0; jb < j1; jb += 32 * U) {
+    float2 r[U], rl[U];
+    float4 w[U];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {                      // loads first: four rows in flight
+    for (int u = 0; u < U; ++u) {
       const int j = jb + u * 32 + lane;
       const bool in = j < j1;
       r[u] = in ? lr[j] : float2{0.f, 0.f};
@@ -278,7 +280,7 @@ __global__ void __launch_bounds__(kLowColsWarps * 32) k_lowmode_cols(const Membe
       w[u] = in ? __ldg(twff + (((step * j) & (ny - 1)) << tshift)) : float4{1.f, 0.f, 0.f, 0.f};
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < U; ++u) {
       float ph, pl;
       ff_mul(r[u].x, w[u].x, w[u].y, ph, pl);          // Re r cos
       ff_add(h[0], l[0], ph, __fmaf_rn(rl[u].x, w[u].x, pl));
