@@ -502,6 +502,8 @@ __device__ __forceinline__ void colpass_chunk_body(const MemberDesc& D, int log2
       mbar_arrive_expect_tx(bar, (two ? 2u : 1u) * ny * 16u);
       bulk_g2s(st0, reinterpret_cast<const float4*>(in0) + (size_t)cb * ny, ny * 16u, bar);
       if (two) bulk_g2s(st1, reinterpret_cast<const float4*>(in1) + (size_t)cb * ny, ny * 16u, bar);
+      // the inertial flow pass reads the chunk's omega_hat^n in its multiply: into L2 now
+      if (KIND == 1 && D.wspec) l2_prefetch(reinterpret_cast<const float4*>(what) + (size_t)cb * ny, ny * 16u);
     }
   };
 
