@@ -244,11 +244,13 @@ __device__ __forceinline__ void ff_mul(float a, float bh, float bl, float& ph, f
 // and the four real sums (Re r cos, Im r sin, Im r cos, Re r sin) are
 // double-float sums (TwoSum), so the result carries essentially only the
 // rounding of the coefficients themselves.  A CTA holds one output; its
-// eight warps share the rows in eighths (lanes coalesced along j, up to 16
-// rows' loads in flight per lane); lanes and warps are folded in a fixed
-// order, as float pairs.
+// eight warps share the rows in eighths (lanes coalesced along j, each lane's
+// rows loaded at once); lanes and warps are folded in a fixed order, as float
+// pairs.
 constexpr int kLowColsWarps = 8;
-constexpr int kLowColsRows = 512;   // rows a warp takes per round (ny = 4096: one round)
+// U rows per lane per round, all their loads in flight at once; the launcher
+// takes U = ny / 256 (one round per warp), 1..16
+template <int U>
 __global__ void __launch_bounds__(kLowColsWarps * 32) k_lowmode_cols(const MemberDesc* __restrict__ descs,
                                                                      int log2ny, const float4* __restrict__ twff) {
   const MemberDesc& D = descs[blockIdx.y];
@@ -267,7 +269,6 @@ __global__ void __launch_bounds__(kLowColsWarps * 32) k_lowmode_cols(const Membe
   // low parts of the coefficients (low == 2: exact Stokes rows), else none
   const float2* lrl = D.low == 2 ? lr + ((size_t)(kLowM + 1) << log2ny) : nullptr;
   float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
-  constexpr int U = kLowColsRows / 32;                 // rows per lane per round, all loads in flight at once
   for (int jb = j0; jb < j1; jb += 32 * U) {
     float2 r[U], rl[U];
     float4 w[U];
@@ -323,7 +324,13 @@ __global__ void __launch_bounds__(kLowColsWarps * 32) k_lowmode_cols(const Membe
 
 void launch_lowmode_cols(const MemberDesc* d, int nmem, int log2ny, const float4* twff, cudaStream_t st) {
   const int outs = (kLowM + 1) * (2 * kLowN + 1);
-  k_lowmode_cols<<<dim3(outs, nmem), kLowColsWarps * 32, 0, st>>>(d, log2ny, twff);
+  const dim3 grid(outs, nmem);
+  const int u = (1 << log2ny) / (kLowColsWarps * 32);
+  if (u >= 16) k_lowmode_cols<16><<<grid, kLowColsWarps * 32, 0, st>>>(d, log2ny, twff);
+  else if (u >= 8) k_lowmode_cols<8><<<grid, kLowColsWarps * 32, 0, st>>>(d, log2ny, twff);
+  else if (u >= 4) k_lowmode_cols<4><<<grid, kLowColsWarps * 32, 0, st>>>(d, log2ny, twff);
+  else if (u >= 2) k_lowmode_cols<2><<<grid, kLowColsWarps * 32, 0, st>>>(d, log2ny, twff);
+  else k_lowmode_cols<1><<<grid, kLowColsWarps * 32, 0, st>>>(d, log2ny, twff);
 }
 
 // The FP32 column pass on single mode columns (ny < 512): item m = one mode,
