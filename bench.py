@@ -24,6 +24,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -94,10 +95,16 @@ def measured_peaks():
 
 
 def sources_sha():
+    """SHA-256 of the kernel sources' code: comments, trailing blanks and empty
+    lines removed, so that a comment edit does not orphan a profile taken on the
+    same code."""
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        lines = [re.sub(r"//.*$", "", line).rstrip() for line in text.splitlines()]
+        h.update("\n".join(line for line in lines if line).encode())
     return h.hexdigest()
 
 

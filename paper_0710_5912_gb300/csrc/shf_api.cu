@@ -1,7 +1,8 @@
 // Host side of the C ABI declared in include/shf.h: grid and ensemble objects,
-// device memory, launch configuration, per-step orchestration (eight launches
-// per step and size class; runs of 100 steps are replayed from a captured CUDA
-// graph), conversions, diagnostics and checkpoints.
+// device memory, launch configuration, per-step orchestration (seven launches
+// per step and size class, each size class of an ensemble on its own stream;
+// runs of 100 steps are replayed from a captured CUDA graph), TMA tensor maps,
+// conversions, diagnostics and checkpoints.
 #include <cmath>
 #include <cstdio>
 #include <cstddef>

@@ -1,6 +1,9 @@
-// Row (x) transforms of a step: k_rowfwd (rowfwd_phi, rowfwd_g) and k_rowinv
-// (rowinv_phi, rowinv_flow), compiled per row length nx = 2^LN.  See
-// step_kernels.cu for the step's kernels and the x-spectral layout.
+// Row (x) passes of a step, compiled per row length nx = 2^LN: k_stage1_rows
+// (the stage-1 stencil fused with the row transforms of phi*, f, omega*),
+// k_rowfwd (mode 1: the stage-2 stencil fused with g's row transform; mode 2:
+// omega's row transform that seeds w_hat) and k_rowinv (rowinv_phi,
+// rowinv_flow; TMA-loaded row pairs).  See step_kernels.cu for the step's
+// kernels and the x-spectral layout.
 #include "step_common.cuh"
 
 namespace shf {
