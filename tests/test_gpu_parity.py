@@ -435,6 +435,32 @@ def test_ensemble_members_match_single_runs(prec):
     ens.close()
 
 
+def test_ensemble_with_tma_rows_and_class_streams_matches_single_runs():
+    """An FP32 ensemble whose two 1024 x 512 members take the TMA-loaded inverse
+    row passes (one tensor map per member) and the chunk column kernel, beside a
+    256^2 member in its own size class (its own stream): every member bit-equal
+    to its single run after 120 steps (one graph replay plus direct launches),
+    across a strain wrap for the sheared 1024 x 512 members."""
+    nxs, nys = [1024, 256, 1024], [512, 256, 512]
+    params = [[1.0, 1.0, 1.0, 1.0, 1.0, 1.0, 2.0, 0.005],
+              [1.0, 1.0, 1.0, 1.0, 1.0, 0.0, 0.01, 0.005],
+              [1.0, 1.0, 1.0, 1.0, 1.0, 0.0, 2.0, 0.005]]
+    ens = shf.Ensemble(nxs, nys, params, seeds=[7, 8, 9], amp=0.2, precision=FP32)
+    ens.step(120)
+    ens.sync()
+    for r in range(3):
+        a, b, kap, M, eta, rho, gdot, dt = params[r]
+        p = oracle.Params(a=a, b=b, kappa=kap, M=M, eta=eta, rho=rho, gdot=gdot, dt=dt)
+        fields = inputs.quench_state(nxs[r], nys[r], 7 + r, 0.2)
+        single = gpu_run(nxs[r], nys[r], FP32, p, fields, 0, 120)
+        got = ens.members[r].get_fields()
+        for name, x, y in zip(("phi", "psi", "omega"), got, single):
+            assert np.array_equal(x, y), f"member {r} {name}"
+        if nxs[r] == 1024:
+            assert ens.members[r].get_time()[3] >= 1        # the strain wrapped
+    ens.close()
+
+
 def c4_ensemble_spec():
     """The batched-ensemble configuration: 96 runs, 32 each of 128^2, 256^2 and
     512^2, rho = r mod 2, gdot log-spaced over 1e-4 .. 3e-2, seed r."""
