@@ -76,11 +76,14 @@ __global__ void k_step_state_init(const MemberDesc* __restrict__ descs, int nmem
 // as double-float pairs; the threads' sums are folded in a fixed order.  The
 // result, hi and lo planes of low_rows, feeds k_lowmode_cols like the
 // compensated sums of the row pass do for the other FP32 members.
-// Work: a CTA takes a tile of up to 32 rows x 64 columns.  phi (halo 2 rows,
-// 3 columns) and mu (halo 1 row, 2 columns) of the tile sit in shared memory;
-// lane r of every warp owns row j0 + r and its warp's slice of the columns,
-// so a thread sums its own row and the twiddle W^{m x} is the same for the
-// whole warp (one broadcast load).  The 8 warps' sums of a row are folded in
+// Work: a CTA takes up to 32 rows x 64 columns of the first half of the rows
+// and the same columns shifted by nx / 2, folded before the DFT: since
+// W^{m (x + nx/2)} = (-1)^m W^{m x}, the terms of both are
+// (F(x) + F(x + nx/2)) W^{m x} for even m and (F(x) - F(x + nx/2)) W^{m x}
+// for odd m, half the products.  phi (halo 2 rows, 3 columns) and mu (halo 1
+// row, 2 columns) of both tiles sit in shared memory; lane r of every warp owns
+// row j0 + r and its warp's slice of the columns, so a thread sums its own row
+// and the twiddle W^{m x} is the same for the whole warp (one broadcast load).  The 8 warps' sums of a row are folded in
 // warp order; with several column tiles per row the CTAs park their sums in
 // a scratch area and the last CTA of a row block to finish (an atomic
 // counter; nothing waits) folds them in tile order into low_rows.
@@ -88,17 +91,19 @@ constexpr int kLxRows = 32;     // rows per CTA: one per lane
 constexpr int kLxCols = 64;     // columns per CTA
 constexpr int kLxWarps = 8;
 constexpr int kLxValues = 2 * (kLowMExact + 1);   // Re and Im of m = 0..kLowMExact
-__host__ __device__ constexpr int lowexact_cols(int nx) { return nx < kLxCols ? nx : kLxCols; }
+// a CTA's tile covers XT columns of the first half of the rows and the same
+// columns shifted by nx / 2 (the DFT folds them: W^{m (x + nx/2)} = (-1)^m W^{m x})
+__host__ __device__ constexpr int lowexact_cols(int nx) { return nx / 2 < kLxCols ? nx / 2 : kLxCols; }
 __host__ __device__ constexpr int lowexact_rows(int ny) { return ny < kLxRows ? ny : kLxRows; }
 __host__ __device__ constexpr int lowexact_pitch_phi(int xt) { return (xt + 6) | 1; }
 __host__ __device__ constexpr int lowexact_pitch_mu(int xt) { return (xt + 4) | 1; }
-__host__ __device__ constexpr int lowexact_smem_floats(int nx, int ny) {
+__host__ __device__ constexpr int lowexact_tile_floats(int nx, int ny) {   // one phi tile and its mu tile
   return (lowexact_rows(ny) + 4) * lowexact_pitch_phi(lowexact_cols(nx)) +
-                 (lowexact_rows(ny) + 2) * lowexact_pitch_mu(lowexact_cols(nx)) >
-                 2 * kLxValues * kLxWarps * kLxRows
-             ? (lowexact_rows(ny) + 4) * lowexact_pitch_phi(lowexact_cols(nx)) +
-                   (lowexact_rows(ny) + 2) * lowexact_pitch_mu(lowexact_cols(nx))
-             : 2 * kLxValues * kLxWarps * kLxRows;
+         (lowexact_rows(ny) + 2) * lowexact_pitch_mu(lowexact_cols(nx));
+}
+__host__ __device__ constexpr int lowexact_smem_floats(int nx, int ny) {
+  return 2 * lowexact_tile_floats(nx, ny) > 2 * kLxValues * kLxWarps * kLxRows ? 2 * lowexact_tile_floats(nx, ny)
+                                                                                : 2 * kLxValues * kLxWarps * kLxRows;
 }
 // acc += F w for an FP32-pair F and a double-float w: the product's rounding
 // error by fused multiply-adds, the low parts added unnormalised
@@ -122,11 +127,14 @@ __global__ void __launch_bounds__(kLxWarps * 32) k_lowrows_exact(const MemberDes
   const int tid = threadIdx.x, nt = blockDim.x;
   const int x0 = blockIdx.x * XT, j0 = blockIdx.y * RT;
   const float* phi = static_cast<const float*>(D.phi);
-  float* tp = sm;                                      // phi rows j0 - 2 + r, cols x0 - 3 + c
-  float* tm = sm + (RT + 4) * PP;                      // mu rows j0 - 1 + r, cols x0 - 2 + c
-  for (int e = tid; e < (RT + 4) * (XT + 6); e += nt) {
-    const int r = e / (XT + 6), c = e - r * (XT + 6);
-    tp[r * PP + c] = __ldg(phi + ((size_t)((j0 - 2 + r) & my) << log2nx) + ((x0 - 3 + c) & mx));
+  // half h = 0, 1: phi rows j0 - 2 + r, cols x0 + h nx/2 - 3 + c; mu rows
+  // j0 - 1 + r, cols x0 + h nx/2 - 2 + c
+  const int TF = lowexact_tile_floats(nx, ny);
+  for (int e = tid; e < 2 * (RT + 4) * (XT + 6); e += nt) {
+    const int h = e / ((RT + 4) * (XT + 6)), e1 = e - h * (RT + 4) * (XT + 6);
+    const int r = e1 / (XT + 6), c = e1 - r * (XT + 6);
+    sm[h * TF + r * PP + c] =
+        __ldg(phi + ((size_t)((j0 - 2 + r) & my) << log2nx) + ((x0 + h * (nx >> 1) - 3 + c) & mx));
   }
   __syncthreads();
   const Shear<float> sc(*D.st, true);                  // s^{n+1}
@@ -135,15 +143,16 @@ __global__ void __launch_bounds__(kLxWarps * 32) k_lowrows_exact(const MemberDes
     const float cxx = 1.f + sc.s * sc.s, cxy = 2.f * sc.s;
     const float kxx = kappa * cxx * (float)D.inv_h2, kxy = kappa * cxy * (float)D.inv_4h2,
                 kyy = kappa * (float)D.inv_h2;
-    for (int e = tid; e < (RT + 2) * (XT + 4); e += nt) {
-      const int r = e / (XT + 4), c = e - r * (XT + 4);
-      const float* pc_ = tp + (r + 1) * PP + (c + 1);  // the centre in the phi tile
+    for (int e = tid; e < 2 * (RT + 2) * (XT + 4); e += nt) {
+      const int h = e / ((RT + 2) * (XT + 4)), e1 = e - h * (RT + 2) * (XT + 4);
+      const int r = e1 / (XT + 4), c = e1 - r * (XT + 4);
+      const float* pc_ = sm + h * TF + (r + 1) * PP + (c + 1);   // the centre in half h's phi tile
       const float pc = pc_[0];
       const float sxx = pc_[1] - 2.f * pc + pc_[-1];
       const float syy = pc_[PP] - 2.f * pc + pc_[-PP];
       const float sxy = pc_[PP + 1] - pc_[-PP + 1] - pc_[PP - 1] + pc_[-PP - 1];
       const float klap = kxx * sxx - kxy * sxy + kyy * syy;
-      tm[r * PM + c] = pc * (b * (pc * pc) - a) - klap;
+      sm[h * TF + (RT + 4) * PP + r * PM + c] = pc * (b * (pc * pc) - a) - klap;
     }
   }
   __syncthreads();
@@ -160,25 +169,30 @@ __global__ void __launch_bounds__(kLxWarps * 32) k_lowrows_exact(const MemberDes
   F2 acc[kLxValues];
 #pragma unroll
   for (int k = 0; k < kLxValues; ++k) acc[k] = F2{0.f, 0.f};
+  // F at (row j, col x) of half h in double-float, p and q pointing at phi and mu there
+  auto curl = [&](const float* p, const float* q) {
+    const F2 dxp = two_sum_f(p[1], -p[-1]);
+    const F2 dxm = two_sum_f(q[1], -q[-1]);
+    const F2 dyp = df_add(df_mul(W0, two_sum_f(p[PP], -p[-PP])), df_mul(W1, two_sum_f(p[PP + dd], -p[-PP - dd])));
+    const F2 dym = df_add(df_mul(W0, two_sum_f(q[PM], -q[-PM])), df_mul(W1, two_sum_f(q[PM + dd], -q[-PM - dd])));
+    return df_mul(df_add(df_mul(dxp, dym), df_neg(df_mul(dyp, dxm))), KF);
+  };
   if (lane < RT) {
-    const float* prow = tp + (lane + 2) * PP + 3;     // phi row j, col 0 of the tile
-    const float* mrow = tm + (lane + 1) * PM + 2;     // mu row j
+    const float* prow = sm + (lane + 2) * PP + 3;                // phi row j, col 0 of half 0's tile
+    const float* mrow = sm + (RT + 4) * PP + (lane + 1) * PM + 2;   // mu row j
     for (int c = c0; c < c1; ++c) {
-      const float* p = prow + c;
-      const float* q = mrow + c;
-      const F2 dxp = two_sum_f(p[1], -p[-1]);
-      const F2 dxm = two_sum_f(q[1], -q[-1]);
-      const F2 dyp = df_add(df_mul(W0, two_sum_f(p[PP], -p[-PP])), df_mul(W1, two_sum_f(p[PP + dd], -p[-PP - dd])));
-      const F2 dym = df_add(df_mul(W0, two_sum_f(q[PM], -q[-PM])), df_mul(W1, two_sum_f(q[PM + dd], -q[-PM - dd])));
-      const F2 F = df_mul(df_add(df_mul(dxp, dym), df_neg(df_mul(dyp, dxm))), KF);
-      df_acc(acc[0], F);
+      const F2 Fa = curl(prow + c, mrow + c);                    // x
+      const F2 Fb = curl(prow + TF + c, mrow + TF + c);          // x + nx / 2
+      const F2 E = df_add(Fa, Fb), O = df_add(Fa, df_neg(Fb));   // for even and odd m
+      df_acc(acc[0], E);
       const int x = x0 + c;
 #pragma unroll
       for (int m = 1; m <= kLowMExact; ++m) {
         if (m > lowm) break;
         const float4 w = __ldg(twff + (((m * x) & mx) << tshift));   // cos, sin of 2 pi m x / nx as pairs
-        df_acc_prod(acc[2 * m], F, w.x, w.y);
-        df_acc_prod(acc[2 * m + 1], F, -w.z, -w.w);
+        const F2 G = (m & 1) ? O : E;
+        df_acc_prod(acc[2 * m], G, w.x, w.y);
+        df_acc_prod(acc[2 * m + 1], G, -w.z, -w.w);
       }
     }
   }
@@ -238,14 +252,14 @@ void launch_lowrows_exact(const MemberDesc* d, int nmem, int log2nx, int log2ny,
                           cudaStream_t st) {
   const int nx = 1 << log2nx, ny = 1 << log2ny;
   const size_t smem = (size_t)lowexact_smem_floats(nx, ny) * sizeof(float);
-  const dim3 grid(nx / lowexact_cols(nx), ny / lowexact_rows(ny), nmem);
+  const dim3 grid((nx / 2) / lowexact_cols(nx), ny / lowexact_rows(ny), nmem);
   k_lowrows_exact<<<grid, kLxWarps * 32, smem, st>>>(d, log2nx, log2ny, twff);
 }
 size_t lowrows_bytes(int nx, int ny) {
   // hi and lo planes of the coefficients, the exact path's per-tile sums and
   // its row-block counters
   return 2 * (size_t)(kLowM + 1) * ny * sizeof(float2) +
-         (size_t)(nx / lowexact_cols(nx)) * kLxValues * ny * sizeof(float2) +
+         (size_t)((nx / 2) / lowexact_cols(nx)) * kLxValues * ny * sizeof(float2) +
          (size_t)(ny / lowexact_rows(ny)) * sizeof(int);
 }
 void launch_step_state_init(const MemberDesc* d, int nmem, cudaStream_t st) {
