@@ -134,7 +134,10 @@ int shf_set_step(shf_grid* g, int64_t n);
 
 /* Advance nsteps >= 0 time steps (Appendix B, items 1-3 or the Stokes
  * algorithm).  Asynchronous on the grid's stream; long runs replay a CUDA
- * graph of up to 100 steps.  On an ensemble every member advances. */
+ * graph of up to 100 steps.  On an ensemble every member advances; each grid
+ * size advances on a stream of the library's own, forked from and joined back
+ * to the grid's stream by events, so work queued on the grid's stream after
+ * this call sees every member's new state. */
 int shf_step(shf_grid* g, int64_t nsteps);
 
 /* Advance nsteps >= 1 steps like shf_step, but launch every kernel directly
@@ -211,7 +214,8 @@ int shf_save(shf_grid* g, const char* path);
 int shf_load(shf_grid* g, const char* path);
 
 /* Ensemble of independent runs (the paper's parameter sweeps, Table I) that
- * advance together, one batched launch per pass and per grid size.
+ * advance together, one batched launch per pass and per grid size (the grid
+ * sizes concurrently, see shf_step).
  * nx[r], ny[r]: as for shf_create_grid; params: nruns rows of
  * (a, b, kappa, M, eta, rho, gdot, dt); dx: nruns spacings or NULL (all 1);
  * seeds: nruns SplitMix64 seeds for the quench state (amplitude amp) or NULL
