@@ -94,17 +94,20 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def code_text(text):
+    """A C++/CUDA source without its comments, trailing blanks and empty lines."""
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    lines = [re.sub(r"//.*$", "", line).rstrip() for line in text.splitlines()]
+    return "\n".join(line for line in lines if line)
+
+
 def sources_sha():
-    """SHA-256 of the kernel sources' code: comments, trailing blanks and empty
-    lines removed, so that a comment edit does not orphan a profile taken on the
-    same code."""
+    """SHA-256 of the kernel sources' code (code_text), so that a comment edit
+    does not orphan a profile taken on the same code."""
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
         with open(os.path.join(ROOT, rel)) as f:
-            text = f.read()
-        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        lines = [re.sub(r"//.*$", "", line).rstrip() for line in text.splitlines()]
-        h.update("\n".join(line for line in lines if line).encode())
+            h.update(code_text(f.read()).encode())
     return h.hexdigest()
 
 
